@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Benchmark of the k-mismatch character-class search on the GENOME workload.
+
+Workload (one step): a 3.1 Gbp order-2 Markov text (41 % GC), coded once and
+resident in HBM (775 MB), searched for three patterns (m = 32, 128, 1024;
+10 % two/three-letter class positions; 100 planted noisy copies each) at
+k = 0, 4 and 16: nine (pattern, k) searches, one scan launch each, then the
+ordering kernels, all through the C ABI.
+
+metric   window-cells/s = sum over the nine searches of (n - m + 1) * m, per
+         second (the paper's nominal count; the early stop of Eq. 4 makes the
+         work far smaller than the count).  Text GB/s = 9 * n/4 bytes per
+         second is reported beside it.
+value    device time of the step (CUDA events on the launching stream), text
+         resident; the text (775 MB) is larger than the 129 MB L2, so no
+         flush is needed between steps.
+e2e      the same metric through the public API with host buffers: every step
+         codes the text from pinned host ASCII (pm_encode_text), compiles the
+         patterns and searches with host output buffers.
+roofline the scan kernel: algorithmic bytes per launch (n/4 text bytes plus
+         8 bytes per hit) over its event-timed duration, against the measured
+         HBM copy bandwidth.
+
+``--impl reference`` times the oracle (plain C, all host cores) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GENOME_N = 3_100_000_000
+MS = (32, 128, 1024)
+KS = (0, 4, 16)
+TEXT_SEED = 3
+METRIC = "window-cells/s"
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=GENOME_N, help="text length per GPU")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--variant", type=int, default=0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- workload --
+
+def genome_patterns():
+    from synth import workloads
+    return workloads.genome_patterns(TEXT_SEED + 8, MS)
+
+
+def build_text(n_local: int, start: int, out: np.ndarray, pats) -> list:
+    """Symbols [start, start + n_local) of the GENOME text with planted copies
+    of every pattern (copies placed by this rank inside its own range)."""
+    import synth
+    synth.markov_text(n_local, TEXT_SEED, out=out, start=start)
+    rng = np.random.default_rng(TEXT_SEED + 16 + start)
+    occ = synth.Occupancy()
+    return [synth.plant(out[:n_local], p, 100, 16, rng, occ) for p in pats]
+
+
+def entries(pats):
+    return [(p, k) for p in pats for k in KS]
+
+
+def cells(n: int, ents) -> int:
+    return sum(max(n - len(p) + 1, 0) * len(p) for p, _ in ents)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle --
+
+def oracle_sample(n: int, pats, budget_s: float, threads: int):
+    """Time the oracle (all host cores) on the first S symbols of the GENOME
+    text, S sized so that the run takes about budget_s seconds."""
+    import oracle
+    import synth
+    ents = entries(pats)
+    maxm = max(MS)
+
+    def run(S):
+        txt = synth.markov_text(S, TEXT_SEED)
+        t0 = time.perf_counter()
+        for p, k in ents:
+            oracle.search(txt, p, k, threads=threads)
+        return time.perf_counter() - t0
+
+    S0 = min(n, 4_000_000)
+    t0 = run(S0)
+    S = int(min(n, max(S0, S0 * budget_s / max(t0, 1e-3))))
+    S = max(S, maxm)
+    t = run(S) if S != S0 else t0
+    return S, t, cells(S, ents) / t
+
+
+# ---------------------------------------------------------------- our arm ---
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    import paper_1611_06115_gb300 as pm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    pats = genome_patterns()
+    ents = entries(pats)
+    maxm = max(len(p) for p in pats)
+    n = a.n
+    # rank r owns windows [r n, (r+1) n) of a world*n text: its piece carries
+    # the m-1 overlap of Sec. 2.6 (weak scaling, no collective on the data path)
+    n_local = n + (maxm - 1 if world > 1 else 0)
+    start = rank * n
+
+    host = torch.empty(n_local, dtype=torch.uint8, pin_memory=True)
+    host_np = host.numpy()
+    t0 = time.perf_counter()
+    planted = build_text(n_local, start, host_np, pats)
+    gen_s = time.perf_counter() - t0
+
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    text = pm.pm_encode_text(host, stream=stream)
+    torch.cuda.synchronize()
+    encode_s = time.perf_counter() - t0
+    cps = [pm.pm_compile_pattern(p) for p in pats]
+    cmap = {p: c for p, c in zip(pats, cps)}
+    handles = [cmap[p] for p, _ in ents]
+    ks = [k for _, k in ents]
+
+    # first search (synchronous) learns the output size and checks the planted copies
+    r = pm.pm_search_ex(text, handles, ks, variant=a.variant)
+    total = r.total
+    per = [r.pattern(i) for i in range(len(ents))]
+    for i, (p, k) in enumerate(ents):
+        found = dict(zip(per[i][0].tolist(), per[i][1].tolist()))
+        pl = planted[pats.index(p)]
+        bad = [(loc, s) for loc, s in pl if s <= k and found.get(loc) != s]
+        if bad:
+            raise SystemExit(f"planted copies missed for m={len(p)} k={k}: {bad[:3]}")
+    cap = int(total * 1.05) + 1024
+    hits_counts = [int(r.offsets[i + 1] - r.offsets[i]) for i in range(len(ents))]
+    del r, per
+
+    n_ev = 2 * len(ents)
+    ev_sets = []
+    for _ in range(a.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+        for e in evs:
+            e.record(stream)
+        ev_sets.append(evs)
+    torch.cuda.synchronize()
+
+    hits_buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    offs_buf = torch.empty(len(ents) + 1, dtype=torch.int64, device=dev)
+
+    def step(evs):
+        return pm_search_into(pm, text, handles, ks, hits_buf, offs_buf, cap, evs, stream,
+                              a.variant)
+
+    warm = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    for e in warm:
+        e.record(stream)
+    for _ in range(max(a.warmup, 3)):
+        step(warm)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(a.steps):
+        step(ev_sets[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / a.steps
+    if world > 1:
+        dist.barrier()
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    got_total = int(offs_buf[-1].item())
+    if got_total != total:
+        raise SystemExit(f"timed searches returned {got_total} hits, expected {total}")
+
+    # per-launch scan durations (event pairs on the launching stream)
+    dur = np.array([[ev_sets[s][2 * e].elapsed_time(ev_sets[s][2 * e + 1])
+                     for e in range(len(ents))] for s in range(a.steps)])
+    mean_ms = dur.mean(axis=0)
+    n_cells = cells(n_local, ents)
+    value = world * cells(n, ents) / (ms / 1e3)
+    text_gbs = world * len(ents) * (n / 4) / (ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    alg_bytes = [n_local / 4 + 8 * h for h in hits_counts]
+    achieved = sum(alg_bytes) / (mean_ms.sum() / 1e3) / 1e9
+
+    # ---- e2e through the public API with host buffers ----
+    e2e_times = []
+    h2d = d2h = 0
+    for it in range(a.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tx = pm.pm_encode_text(host, stream=stream)
+        cc = [pm.pm_compile_pattern(p) for p in pats]
+        cm = {p: c for p, c in zip(pats, cc)}
+        rr = pm.pm_search_ex(tx, [cm[p] for p, _ in ents], ks, capacity=cap, out="host",
+                             stream=stream, variant=a.variant)
+        tot = rr.total
+        dt = time.perf_counter() - t0
+        if it > 0:
+            e2e_times.append(dt)
+        h2d = n_local + sum(16 * ((len(p) + 31) // 32) for p in pats) + 16 * len(ents)
+        d2h = 8 * tot + 8 * (len(ents) + 1)
+        del tx, rr
+    e2e_s = statistics.median(e2e_times)
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * cells(n, ents) / e2e_s
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "window-cells/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": max(a.warmup, 3),
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic: seeded order-2 Markov text, 41% GC, planted noisy copies "
+                "(stands in for GRCh37 chr2)",
+        "config": {
+            "workload": "GENOME: n=3.1e9 per GPU, m in {32,128,1024} (10% classes), "
+                        "k in {0,4,16}, 100 planted copies per pattern; 9 searches per step",
+            "n_per_gpu": n, "patterns_m": list(MS), "ks": list(KS),
+            "searches_per_step": len(ents), "launch": "one scan launch per (pattern, k)",
+            "l2": "inputs larger than L2 (775 MB packed text vs 129 MB L2); no flush",
+            "parallelism": f"text shards with m-1 overlap x{world}",
+            "variant": {0: "auto", 1: "pattern-sliced", 2: "window-sliced"}[a.variant],
+        },
+        "text_gbs": text_gbs,
+        "gbp_per_s": world * len(ents) * n / (ms / 1e3) / 1e9,
+        "hits_per_step": total,
+        "e2e": {"value": e2e_value, "unit": "window-cells/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+                "what": "pm_encode_text(pinned host ASCII) + pm_compile_pattern + "
+                        "pm_search(host outputs), every step"},
+        "gpu_launches": a.steps * (len(ents) + 5),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_scan (all nine launches)",
+                     "per_launch_ms": {f"m={len(p)},k={k}": float(t)
+                                       for (p, k), t in zip(ents, mean_ms)}},
+        "clocks": ck,
+        "setup_s": {"generate": gen_s, "encode": encode_s,
+                    "encode_gbs": n_local / encode_s / 1e9},
+    }
+    if rank == 0 and world == 1:
+        S, t, v = oracle_sample(n, pats, a.cpu_seconds, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": v, "unit": "window-cells/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"first {S} symbols of the same text, all nine "
+                                          f"(pattern, k) searches, {t:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def pm_search_into(pm, text, handles, ks, hits, offs, cap, evs, stream, variant):
+    """One step: pm_search_ex into preallocated device buffers, asynchronous."""
+    import ctypes
+    from paper_1611_06115_gb300 import _native as N
+    npat = len(handles)
+    harr = (ctypes.c_void_p * npat)(*[h.handle for h in handles])
+    karr = (ctypes.c_int32 * npat)(*ks)
+    earr = (ctypes.c_void_p * len(evs))(*[e.cuda_event for e in evs])
+    opts = N.pm_options(variant, 0, ctypes.cast(earr, ctypes.POINTER(ctypes.c_void_p)))
+    st = N.lib().pm_search_ex(text.handle, harr, npat, karr, ctypes.c_void_p(hits.data_ptr()), cap,
+                              ctypes.c_void_p(offs.data_ptr()), None, ctypes.byref(opts),
+                              ctypes.c_void_p(stream.cuda_stream))
+    N.check(st, "pm_search_ex")
+
+
+# ---------------------------------------------------------- reference arm ---
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    pats = genome_patterns()
+    ents = entries(pats)
+    threads = os.cpu_count() or 1
+    budget = 150.0  # seconds for the whole run
+    steps_total = a.steps + max(a.warmup, 3)
+    S0 = 2_000_000
+    txt0 = synth.markov_text(S0, TEXT_SEED)
+    t0 = time.perf_counter()
+    for p, k in ents:
+        oracle.search(txt0, p, k, threads=threads)
+    t_probe = time.perf_counter() - t0
+    per_step = budget / steps_total
+    S = int(max(max(MS), min(a.n, S0 * per_step / max(t_probe, 1e-4))))
+    txt = synth.markov_text(S, TEXT_SEED)
+
+    def step():
+        for p, k in ents:
+            oracle.search(txt, p, k, threads=threads)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = (time.perf_counter() - t0) / a.steps
+    v = cells(S, ents) / dt
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": v, "unit": "window-cells/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": max(a.warmup, 3), "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic: seeded order-2 Markov text, 41% GC",
+        "config": {"workload": "GENOME recipe, bounded sample: first "
+                               f"{S} symbols of the 3.1e9 text, m in {{32,128,1024}}, "
+                               "k in {0,4,16}; 9 searches per step",
+                   "sample_symbols": S},
+        "cpu_baseline": {"value": v, "unit": "window-cells/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {S} symbols per step"},
+        "e2e": {"value": v, "unit": "window-cells/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

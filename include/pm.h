@@ -1,0 +1,198 @@
+/*
+ * pm.h -- C ABI of libpm: k-mismatch matching of IUPAC character-class
+ * patterns against a 2-bit DNA text, on one GB300 GPU (sm_103a).
+ *
+ * Method: "Fast low-level pattern matching algorithm" (Soldo, Krzic, Sersic,
+ * arXiv 1611.06115).  Location i of text t holds pattern p with at most k
+ * mismatches when  sum_{j=1..m} L[(p[j] << 2) OR t[i+j-1]] <= k  (Eq. 4),
+ * where t is coded by Table 1, p by Table 2, and L is the 64-entry
+ * match/mismatch dictionary of Table 3 that the paper derives from the
+ * prime-residue test of Sec. 1.3 (Eq. 1 and Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Locations are 0-based (the paper's location i is ours + 1).  A text
+ *     of n symbols has n-m+1 windows; no window is partial; m > n gives none.
+ *   - k is inclusive (Eq. 4 reads "<= k"); k >= m reports every window.
+ *   - Errors are returned as pm_status, never thrown.  pm_status_string()
+ *     names a status; pm_last_error() gives the calling thread's last
+ *     detailed message (for example the offset of a bad text symbol).
+ *   - "stream" is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  Work is ordered on that stream.
+ *   - Pointers documented as "host or device" are classified with
+ *     cudaPointerGetAttributes: device (and managed) memory is used in
+ *     place, anything else is treated as host memory.
+ *   - Handles (pm_text, pm_pattern, pm_batch) are owned by the library and
+ *     released with the matching *_free call.  Buffers passed in are owned
+ *     by the caller.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pm_status;
+
+#define PM_OK 0
+#define PM_E_ARG (-1)       /* an argument is invalid (NULL, m == 0, k < 0, ...) */
+#define PM_E_SYMBOL (-2)    /* a text symbol is not one of A C G T (either case) */
+#define PM_E_NOMEM (-3)     /* a device or host allocation failed */
+#define PM_E_OVERFLOW (-4)  /* more hits than the caller's capacity */
+#define PM_E_TOO_LARGE (-5) /* n >= 2^32, or a size limit of this build */
+#define PM_E_TIMEOUT (-6)   /* a bounded wait inside a kernel gave up */
+#define PM_E_CUDA (-7)      /* a CUDA runtime call failed */
+
+/* One reported window: 0-based location and its exact mismatch count. */
+typedef struct pm_hit {
+    uint32_t location;
+    uint32_t mismatches;
+} pm_hit;
+
+typedef struct pm_text pm_text;       /* device-resident 2-bit text */
+typedef struct pm_pattern pm_pattern; /* compiled pattern (host data) */
+typedef struct pm_batch pm_batch;     /* patterns + k + scratch, resident on the device */
+
+/* Value of offsets[npat] that signals a device-side failure (a timed-out
+ * wait) to callers that did not ask for a synchronous status. */
+#define PM_TOTAL_ERROR UINT64_MAX
+
+/* ------------------------------------------------------------------ text */
+
+/*
+ * pm_encode_text -- text coding of Sec. 2.1 (Table 1: A=00 C=01 G=10 T=11).
+ *
+ * ascii   n bytes, host or device.  A C G T in either case; any other byte
+ *         is an error (PM_E_SYMBOL; pm_last_error() names its offset).
+ * n       number of symbols, 0 <= n < 2^32 (larger: PM_E_TOO_LARGE).
+ * stream  the copy (for host input) and the coding kernel run on it.
+ * out     receives a new handle.  The coded text lives in device memory on
+ *         the current device: two bit planes (low and high code bit), 32
+ *         symbols per 32-bit word, 2 bits per symbol in total.
+ *
+ * The call returns after the coding has finished (it synchronises the
+ * stream to check the symbols).  Host input is copied in pieces through a
+ * device staging buffer, so the ASCII text never has to fit on the device.
+ */
+pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **out);
+
+/* Number of symbols of an encoded text. */
+uint64_t pm_text_length(const pm_text *text);
+
+/* Device address and size in bytes of the coded planes (read-only view for
+ * callers that want to inspect the layout); either out pointer may be NULL. */
+pm_status pm_text_device_planes(const pm_text *text, const void **planes, uint64_t *bytes);
+
+void pm_text_free(pm_text *text);
+
+/* --------------------------------------------------------------- pattern */
+
+/*
+ * pm_compile_pattern -- pattern coding of Sec. 2.2 (Table 2).
+ *
+ * iupac   m bytes (host) over the IUPAC letters A C G T M R W S Y K V H D B N
+ *         and "-", either case.  Any other byte is coded 1111 ("-", which
+ *         mismatches every letter), as Sec. 2.2 prescribes; the number of
+ *         such bytes is reported by pm_pattern_unknown().
+ * m       pattern length, 1 <= m <= PM_MAX_PATTERN.
+ * out     receives a new handle (host memory only).
+ *
+ * Each class becomes a 4-bit membership mask obtained from the residue test
+ * of Sec. 1.3 (letter a is in class S iff e_a * n_S = 0 mod M, Eq. 1 and
+ * Eq. 3), i.e. exactly the rows of Table 3.
+ */
+#define PM_MAX_PATTERN (1u << 24)
+pm_status pm_compile_pattern(const char *iupac, uint32_t m, pm_pattern **out);
+
+uint32_t pm_pattern_length(const pm_pattern *pattern);
+uint32_t pm_pattern_unknown(const pm_pattern *pattern);
+
+/* Copy the compiled membership masks to host memory: for chunk c (pattern
+ * positions 32c .. 32c+31), out[4c+0..3] are the A, C, G, T words; bit b of
+ * the A word is 1 iff A belongs to the class at position 32c+b (Table 3
+ * entry 0).  Positions past m read as members of every class.  words must be
+ * at least 4*ceil(m/32).  Host only; no device work. */
+pm_status pm_pattern_masks(const pm_pattern *pattern, uint32_t *out, uint64_t words);
+
+void pm_pattern_free(pm_pattern *pattern);
+
+/* ---------------------------------------------------------------- search */
+
+/*
+ * pm_search -- Eq. 4 for every window of the text and every pattern
+ * (Sec. 2.4), the sum stopping once it exceeds k (Sec. 2.4-2.5), the text
+ * split into tiles with an m-1 overlap (Sec. 2.6).  One kernel launch per
+ * pattern.
+ *
+ * text      encoded text.
+ * patterns  host array of npat compiled patterns (the same handle may
+ *           appear several times, e.g. with different k).
+ * npat      number of patterns, 0 <= npat <= PM_MAX_BATCH.
+ * k         host array of npat values, each >= 0.
+ * hits      output, capacity records, host or device.
+ * capacity  number of records hits can hold.
+ * offsets   output, npat+1 values, host or device (same kind as hits).
+ *           Pattern p's hits are hits[offsets[p] .. offsets[p+1]), sorted
+ *           by location; offsets[npat] is the total.
+ * needed    optional host pointer.  When given, the call waits for the
+ *           result, stores the total number of hits there and returns
+ *           PM_E_OVERFLOW if it exceeds capacity.
+ * stream    all device work is ordered on it.
+ *
+ * With device buffers and needed == NULL the call is asynchronous: it
+ * returns once the work is queued, and the caller reads offsets[npat] after
+ * the stream to learn the total.  With host buffers the call waits.
+ *
+ * If the total exceeds capacity, offsets still hold every pattern's count
+ * and no hit record is written.  A device-side failure makes offsets[npat]
+ * equal PM_TOTAL_ERROR (and the synchronous forms return PM_E_TIMEOUT).
+ * Scratch memory is taken from the stream-ordered pool of the current
+ * device (cudaMallocAsync) and released on the stream before returning.
+ */
+#define PM_MAX_BATCH (1u << 16)
+pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                    const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                    uint64_t *needed, void *stream);
+
+/*
+ * pm_search_ex -- pm_search with tuning and measurement options.  Results
+ * are identical for every choice of options.
+ *
+ * variant   how the first 32 pattern positions are evaluated:
+ *           PM_VARIANT_PATTERN_SLICED  one window per word, __popc counts;
+ *           PM_VARIANT_WINDOW_SLICED   32 windows per word, bit-sliced
+ *                                      counter (only for k <= 31; larger k
+ *                                      falls back to pattern-sliced);
+ *           PM_VARIANT_AUTO            chosen per pattern from k.
+ * grid      CTAs per scan launch; 0 means as many as the device keeps
+ *           resident at once.
+ * events    NULL, or 2*npat cudaEvent_t handles (created by the caller on
+ *           the current device); events[2p] and events[2p+1] are recorded on
+ *           the stream just before and just after pattern p's scan kernel.
+ */
+#define PM_VARIANT_AUTO 0
+#define PM_VARIANT_PATTERN_SLICED 1
+#define PM_VARIANT_WINDOW_SLICED 2
+typedef struct pm_options {
+    int32_t variant;
+    int32_t grid;
+    void *const *events;
+} pm_options;
+
+pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                       const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                       uint64_t *needed, const pm_options *options, void *stream);
+
+/* ---------------------------------------------------------------- status */
+
+const char *pm_status_string(pm_status status);
+const char *pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

@@ -1,0 +1,204 @@
+// Internal declarations of libpm (not part of the public ABI).
+//
+// Device layout of a coded text (Sec. 2.1, Table 1): symbol s has the 2-bit
+// code A=00 C=01 G=10 T=11.  Symbols are grouped in blocks of 32; block b is
+// one uint2 {lo, hi} whose bit w holds the low / high code bit of symbol
+// 32*b + w.  The planes end with kPadBlocks zero blocks (symbol "A") so that
+// every tile copy and every window read stays inside the allocation; windows
+// that would use padding are never reported.
+//
+// Device layout of a compiled pattern (Sec. 2.2, Table 2): chunk c covers
+// positions 32c .. 32c+31 and is one uint4 {A, C, G, T} of membership masks:
+// bit b of the A word is set iff text letter A lies in the class of position
+// 32c+b (Table 3 holds 0 for that pair).  Positions past m have all four bits
+// set, so they never count as a mismatch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pm.h"
+
+struct pm_text {
+    uint64_t n;        // symbols
+    uint64_t nblocks;  // allocated blocks, padding included
+    uint2 *planes;     // device
+    int device;
+};
+
+struct pm_pattern {
+    uint32_t m;
+    uint32_t nchunks;
+    uint32_t unknown;  // symbols coded "-" because Table 2 does not list them
+    uint4 *masks;      // host, nchunks entries
+};
+
+namespace pm {
+
+constexpr int kScanThreads = 256;                        // threads per scan CTA
+constexpr uint64_t kTileBlocks = kScanThreads;           // one block per thread
+constexpr uint64_t kTileWindows = 32ull * kTileBlocks;   // windows per tile
+constexpr int kHaloBlocks = 2;                           // staged after the tile
+constexpr uint32_t kTileBytes = (uint32_t)((kTileBlocks + kHaloBlocks) * sizeof(uint2));
+constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
+constexpr uint64_t kWaitLimitNs = 1000000000ull;         // bounded device waits: 1 s
+
+static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// One pattern of a search, as the kernels see it.
+struct PatDesc {
+    uint32_t m;        // pattern length
+    uint32_t nchunks;  // ceil(m / 32)
+    int32_t k;         // allowed mismatches (>= 0)
+    uint32_t pad0;
+    uint64_t masks;    // index of chunk 0 in the mask arena (uint4 units)
+    uint64_t nwin;     // windows: n - m + 1, or 0 when m > n
+    uint64_t tile0;    // first tile-table entry of this pattern
+    uint64_t ntiles;   // ceil(nwin / kTileWindows)
+};
+
+// Hits of one (pattern, tile): where the scan kernel put them in the
+// scratch hit buffer, and how many.  Within a tile they are in window order.
+struct TileEntry {
+    unsigned long long src;
+    uint32_t count;
+    uint32_t pad0;
+};
+
+// Device status bits written by kernels.
+constexpr uint32_t kDevTimeout = 1u;
+
+// Scan-kernel variants.
+enum class Variant : int {
+    kPatternSliced = 0,  // per window, 32 positions per word, popc
+    kWindowSliced = 1,   // per position, 32 windows per word, bit-sliced counter
+};
+
+// Launch one scan kernel for one pattern (pm_scan.cu).
+cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *masks,
+                        TileEntry *table, pm_hit *tmp, uint64_t cap, unsigned long long *cursor,
+                        uint32_t *status, int grid, cudaStream_t stream);
+
+// Number of resident scan CTAs the device runs at once (pm_scan.cu).
+int scan_grid_limit(Variant v, int device);
+
+// Window-sliced counter width for k, or -1 if k is too large for it.
+int ws_bits(int32_t k);
+
+// Ordering: exclusive scan of table counts, per-pattern CSR offsets, and the
+// gather of hits into their final places (pm_order.cu).  Needs
+// order_scratch_bytes(entries) bytes of scratch.
+size_t order_scratch_bytes(uint64_t entries);
+cudaError_t launch_order(const TileEntry *table, uint64_t entries, const uint64_t *pat_tile0,
+                         uint32_t npat, const pm_hit *tmp, pm_hit *hits, uint64_t cap,
+                         uint64_t *offsets, const uint32_t *status, void *scratch,
+                         cudaStream_t stream);
+
+// Text coding kernel (pm_text.cu).
+cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol,
+                        uint2 *planes, unsigned long long *bad, cudaStream_t stream);
+
+// Thread-local detailed error message.
+void set_error(const char *fmt, ...);
+pm_status cuda_status(cudaError_t e, const char *what);
+
+// Classify a pointer: true if the device can use it in place.
+bool is_device_pointer(const void *p);
+
+}  // namespace pm
+
+// ---------------------------------------------------------------- device ----
+#ifdef __CUDACC__
+namespace pm {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk (TMA) copy global -> shared, completing on an mbarrier.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete, giving up after
+// limit_ns nanoseconds of wall time.  Returns false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// Bitwise select: bits of a where c is 1, bits of b where c is 0.
+__device__ __forceinline__ uint32_t sel(uint32_t c, uint32_t a, uint32_t b)
+{
+    return (c & a) | (~c & b);
+}
+
+// Table 3 evaluated on 32 (pattern position, text symbol) pairs at once.
+// (lo, hi) are the text code bits, M the membership masks {A, C, G, T} of
+// the 32 positions; returns 1 where the pair matches (L = 0).
+__device__ __forceinline__ uint32_t class_match(uint32_t lo, uint32_t hi, uint4 M)
+{
+    return sel(hi, sel(lo, M.w, M.z), sel(lo, M.y, M.x));
+}
+
+}  // namespace dev
+}  // namespace pm
+#endif

@@ -1,0 +1,175 @@
+// Ordering of hits (output contract: per pattern, sorted by location).
+//
+// The scan kernels leave each (pattern, tile) segment of hits in window
+// order somewhere in a scratch buffer and record {where, how many} in a
+// tile table whose entries run pattern-major, tile-minor, i.e. already in
+// the output order.  An exclusive prefix sum over the table's counts gives
+// each segment its final place; per-pattern CSR offsets are the prefix at
+// each pattern's first entry; a gather copies the segments.  No comparison
+// sort is needed.
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+constexpr int kOrdThreads = 256;
+constexpr int kOrdItems = 16;
+constexpr uint64_t kSeg = (uint64_t)kOrdThreads * kOrdItems;  // entries per block
+
+// Exclusive prefix sum over a CTA; returns this thread's prefix and sets
+// *total to the CTA sum.
+__device__ __forceinline__ unsigned long long block_exclusive(unsigned long long v,
+                                                              unsigned long long *total)
+{
+    __shared__ unsigned long long sw[kOrdThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int q = 0; q < kOrdThreads / 32; ++q) {
+            const unsigned long long t = sw[q];
+            sw[q] = run;
+            run += t;
+        }
+        *total = run;  // the caller passes a __shared__ variable
+    }
+    __syncthreads();
+    const unsigned long long r = sw[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kOrdThreads)
+    k_reduce(const TileEntry *__restrict__ table, uint64_t entries,
+             unsigned long long *__restrict__ partial)
+{
+    __shared__ unsigned long long stotal;
+    const uint64_t base = (uint64_t)blockIdx.x * kSeg + (uint64_t)threadIdx.x * kOrdItems;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kOrdItems; ++i)
+        if (base + i < entries) s += table[base + i].count;
+    block_exclusive(s, &stotal);
+    if (threadIdx.x == 0) partial[blockIdx.x] = stotal;
+}
+
+// One CTA: exclusive scan of the per-block partials in place; total at [n].
+__global__ void __launch_bounds__(kOrdThreads)
+    k_scan_partials(unsigned long long *__restrict__ partial, uint64_t n)
+{
+    __shared__ unsigned long long stotal;
+    unsigned long long carry = 0;
+    for (uint64_t off = 0; off < n; off += kOrdThreads) {
+        const uint64_t i = off + threadIdx.x;
+        const unsigned long long v = i < n ? partial[i] : 0ull;
+        const unsigned long long e = block_exclusive(v, &stotal);
+        if (i < n) partial[i] = carry + e;
+        carry += stotal;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[n] = carry;
+}
+
+__global__ void __launch_bounds__(kOrdThreads)
+    k_dest(const TileEntry *__restrict__ table, uint64_t entries,
+           const unsigned long long *__restrict__ partial, unsigned long long *__restrict__ dest)
+{
+    __shared__ unsigned long long stotal;
+    const uint64_t base = (uint64_t)blockIdx.x * kSeg + (uint64_t)threadIdx.x * kOrdItems;
+    uint32_t c[kOrdItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kOrdItems; ++i) {
+        c[i] = base + i < entries ? table[base + i].count : 0u;
+        s += c[i];
+    }
+    unsigned long long run = partial[blockIdx.x] + block_exclusive(s, &stotal);
+#pragma unroll
+    for (int i = 0; i < kOrdItems; ++i) {
+        if (base + i < entries) dest[base + i] = run;
+        run += c[i];
+    }
+}
+
+__global__ void k_offsets(const uint64_t *__restrict__ pat_tile0, uint32_t npat, uint64_t entries,
+                          const unsigned long long *__restrict__ dest,
+                          const unsigned long long *__restrict__ total,
+                          const uint32_t *__restrict__ status, uint64_t *__restrict__ offsets)
+{
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > npat) return;
+    if (p == npat) {
+        offsets[p] = (*status & kDevTimeout) ? PM_TOTAL_ERROR : (uint64_t)*total;
+        return;
+    }
+    const uint64_t e = pat_tile0[p];
+    offsets[p] = e < entries ? (uint64_t)dest[e] : (uint64_t)*total;
+}
+
+// One warp per table entry: copy its segment to its final place.
+__global__ void __launch_bounds__(kOrdThreads)
+    k_gather(const TileEntry *__restrict__ table, uint64_t entries,
+             const unsigned long long *__restrict__ dest, const unsigned long long *__restrict__ total,
+             const uint32_t *__restrict__ status, const pm_hit *__restrict__ tmp,
+             pm_hit *__restrict__ hits, uint64_t cap)
+{
+    if (*total > cap || (*status & kDevTimeout)) return;
+    const uint64_t warps = (uint64_t)gridDim.x * (kOrdThreads / 32);
+    const int lane = threadIdx.x & 31;
+    for (uint64_t e = (uint64_t)blockIdx.x * (kOrdThreads / 32) + (threadIdx.x >> 5); e < entries;
+         e += warps) {
+        const TileEntry te = table[e];
+        if (te.count == 0) continue;
+        const unsigned long long d = dest[e];
+        for (uint32_t i = lane; i < te.count; i += 32) hits[d + i] = tmp[te.src + i];
+    }
+}
+
+}  // namespace
+
+size_t order_scratch_bytes(uint64_t entries)
+{
+    const uint64_t nblk = (entries + kSeg - 1) / kSeg;
+    // partials (+1 for the total) and per-entry destinations
+    return (size_t)((nblk + 1) * 8 + entries * 8 + 256);
+}
+
+cudaError_t launch_order(const TileEntry *table, uint64_t entries, const uint64_t *pat_tile0,
+                         uint32_t npat, const pm_hit *tmp, pm_hit *hits, uint64_t cap,
+                         uint64_t *offsets, const uint32_t *status, void *scratch,
+                         cudaStream_t stream)
+{
+    const uint64_t nblk = (entries + kSeg - 1) / kSeg;
+    auto *partial = (unsigned long long *)scratch;
+    auto *dest = partial + nblk + 1;
+    const unsigned long long *total = partial + nblk;
+    if (nblk > 0) {
+        k_reduce<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, entries, partial);
+    }
+    k_scan_partials<<<1, kOrdThreads, 0, stream>>>(partial, nblk);
+    if (nblk > 0) {
+        k_dest<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, entries, partial, dest);
+    }
+    k_offsets<<<(npat + 1 + 255) / 256, 256, 0, stream>>>(pat_tile0, npat, entries, dest, total,
+                                                          status, offsets);
+    if (entries > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        uint64_t want = (entries + (kOrdThreads / 32) - 1) / (kOrdThreads / 32);
+        uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
+        if (grid < 1) grid = 1;
+        k_gather<<<(unsigned)grid, kOrdThreads, 0, stream>>>(table, entries, dest, total, status,
+                                                             tmp, hits, cap);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -1,0 +1,255 @@
+// pm_search: one scan launch per pattern, then the ordering kernels.
+//
+// Per call, the host builds one descriptor per (pattern, k) pair, packs the
+// patterns' chunk masks into one arena (a pattern handle that appears more
+// than once is packed once), and uploads arena and per-pattern tile offsets
+// through a small ring of pinned host buffers so that the upload is a true
+// asynchronous copy.  Scratch comes from the current device's stream-ordered
+// pool (cudaMallocAsync) and goes back to it on the same stream.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+constexpr int kRing = 4;
+constexpr int kMaxDevices = 64;
+
+struct PinnedSlot {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+std::mutex g_ring_mu;
+PinnedSlot g_ring[kMaxDevices][kRing];
+int g_ring_next[kMaxDevices];
+
+// A pinned host buffer of at least `bytes`, free of earlier copies.  The
+// caller must call release_pinned() after queueing its copy from it.
+pm_status acquire_pinned(int dev, size_t bytes, PinnedSlot **out)
+{
+    std::lock_guard<std::mutex> lk(g_ring_mu);
+    PinnedSlot &s = g_ring[dev][g_ring_next[dev]++ % kRing];
+    if (s.pending) {
+        cudaEventSynchronize(s.done);
+        s.pending = false;
+    }
+    if (!s.done) {
+        pm_status rc = cuda_status(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming),
+                                   "cudaEventCreate");
+        if (rc) return rc;
+    }
+    if (s.cap < bytes) {
+        if (s.ptr) cudaFreeHost(s.ptr);
+        s.ptr = nullptr;
+        s.cap = 0;
+        const size_t want = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+        pm_status rc = cuda_status(cudaHostAlloc(&s.ptr, want, cudaHostAllocPortable), "cudaHostAlloc");
+        if (rc) return rc;
+        s.cap = want;
+    }
+    *out = &s;
+    return PM_OK;
+}
+
+void release_pinned(PinnedSlot *s, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_ring_mu);
+    if (cudaEventRecord(s->done, st) == cudaSuccess) s->pending = true;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                       const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                       uint64_t *needed, const pm_options *opts, void *stream)
+{
+    if (!text || !offsets || (npat > 0 && (!patterns || !k)) || (capacity > 0 && !hits)) {
+        set_error("pm_search: NULL argument");
+        return PM_E_ARG;
+    }
+    if (npat > PM_MAX_BATCH) {
+        set_error("pm_search: npat = %u exceeds %u", npat, PM_MAX_BATCH);
+        return PM_E_TOO_LARGE;
+    }
+    for (uint32_t p = 0; p < npat; ++p) {
+        if (!patterns[p] || k[p] < 0) {
+            set_error("pm_search: pattern %u is NULL or has k < 0", p);
+            return PM_E_ARG;
+        }
+    }
+    const pm_options o = opts ? *opts : pm_options{};
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != text->device) {
+        set_error("pm_search: text lives on device %d, current device is %d", text->device, dev);
+        return PM_E_ARG;
+    }
+    const bool dev_out = is_device_pointer(offsets);
+    if (capacity > 0 && is_device_pointer(hits) != dev_out) {
+        set_error("pm_search: hits and offsets must both be host or both be device memory");
+        return PM_E_ARG;
+    }
+
+    // ---- descriptors and the mask arena ----
+    std::vector<PatDesc> desc(npat);
+    std::unordered_map<const pm_pattern *, uint64_t> where;
+    uint64_t nmask = 0, entries = 0;
+    for (uint32_t p = 0; p < npat; ++p) {
+        const pm_pattern *pt = patterns[p];
+        auto it = where.find(pt);
+        uint64_t mo;
+        if (it == where.end()) {
+            mo = nmask;
+            where.emplace(pt, mo);
+            nmask += pt->nchunks;
+        } else {
+            mo = it->second;
+        }
+        PatDesc &d = desc[p];
+        d.m = pt->m;
+        d.nchunks = pt->nchunks;
+        d.k = k[p];
+        d.pad0 = 0;
+        d.masks = mo;
+        d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
+        d.tile0 = entries;
+        d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
+        entries += d.ntiles;
+    }
+
+    // ---- scratch layout ----
+    const size_t sz_masks = align256(nmask * sizeof(uint4));
+    const size_t sz_tile0 = align256((npat + 1) * sizeof(uint64_t));
+    const size_t sz_table = align256(entries * sizeof(TileEntry));
+    const size_t sz_tmp = align256(capacity * sizeof(pm_hit));
+    const size_t sz_ctl = 256;  // cursor + status
+    const size_t sz_order = align256(order_scratch_bytes(entries));
+    const size_t sz_out = dev_out ? 0 : align256(capacity * sizeof(pm_hit)) +
+                                            align256((npat + 1) * sizeof(uint64_t));
+    const size_t total_bytes = sz_masks + sz_tile0 + sz_table + sz_tmp + sz_ctl + sz_order + sz_out;
+
+    char *scratch = nullptr;
+    pm_status rc = cuda_status(cudaMallocAsync((void **)&scratch, total_bytes, st), "cudaMallocAsync scratch");
+    if (rc) return rc;
+    char *cur = scratch;
+    auto take = [&](size_t b) { char *r = cur; cur += b; return r; };
+    uint4 *d_masks = (uint4 *)take(sz_masks);
+    uint64_t *d_tile0 = (uint64_t *)take(sz_tile0);
+    TileEntry *d_table = (TileEntry *)take(sz_table);
+    pm_hit *d_tmp = (pm_hit *)take(sz_tmp);
+    char *ctl = take(sz_ctl);
+    unsigned long long *d_cursor = (unsigned long long *)ctl;
+    uint32_t *d_status = (uint32_t *)(ctl + 8);
+    void *d_order = take(sz_order);
+    pm_hit *d_hits = hits;
+    uint64_t *d_offsets = offsets;
+    if (!dev_out) {
+        d_hits = (pm_hit *)take(align256(capacity * sizeof(pm_hit)));
+        d_offsets = (uint64_t *)take(align256((npat + 1) * sizeof(uint64_t)));
+    }
+
+    // ---- upload masks and tile offsets through pinned memory ----
+    const size_t up_bytes = nmask * sizeof(uint4) + (npat + 1) * sizeof(uint64_t);
+    PinnedSlot *slot = nullptr;
+    rc = acquire_pinned(dev, up_bytes, &slot);
+    if (!rc) {
+        char *h = (char *)slot->ptr;
+        for (const auto &kv : where)
+            std::memcpy(h + kv.second * sizeof(uint4), kv.first->masks, kv.first->nchunks * sizeof(uint4));
+        uint64_t *ht0 = (uint64_t *)(h + nmask * sizeof(uint4));
+        for (uint32_t p = 0; p < npat; ++p) ht0[p] = desc[p].tile0;
+        ht0[npat] = entries;
+        rc = cuda_status(cudaMemcpyAsync(d_masks, h, nmask * sizeof(uint4), cudaMemcpyHostToDevice, st),
+                         "upload masks");
+        if (!rc)
+            rc = cuda_status(cudaMemcpyAsync(d_tile0, ht0, (npat + 1) * sizeof(uint64_t),
+                                             cudaMemcpyHostToDevice, st),
+                             "upload tile offsets");
+        release_pinned(slot, st);
+    }
+    if (!rc) rc = cuda_status(cudaMemsetAsync(ctl, 0, sz_ctl, st), "memset control words");
+
+    // ---- one scan launch per pattern ----
+    for (uint32_t p = 0; !rc && p < npat; ++p) {
+        Variant v;
+        if (o.variant == PM_VARIANT_PATTERN_SLICED) v = Variant::kPatternSliced;
+        else if (o.variant == PM_VARIANT_WINDOW_SLICED) v = Variant::kWindowSliced;
+        else v = ws_bits(desc[p].k) >= 0 && ws_bits(desc[p].k) <= 2 ? Variant::kWindowSliced
+                                                                     : Variant::kPatternSliced;
+        const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, dev);
+        if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p], st);
+        rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
+                                     d_cursor, d_status, grid, st),
+                         "scan kernel");
+        if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p + 1], st);
+    }
+    if (!rc)
+        rc = cuda_status(launch_order(d_table, entries, d_tile0, npat, d_tmp, d_hits, capacity,
+                                      d_offsets, d_status, d_order, st),
+                         "order kernels");
+
+    uint64_t total = 0;
+    bool waited = false;
+    if (!rc && !dev_out) {
+        rc = cuda_status(cudaMemcpyAsync(offsets, d_offsets, (npat + 1) * sizeof(uint64_t),
+                                         cudaMemcpyDeviceToHost, st),
+                         "copy offsets");
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
+        waited = true;
+        total = offsets[npat];
+        if (!rc && total != PM_TOTAL_ERROR && total <= capacity && total > 0) {
+            rc = cuda_status(cudaMemcpyAsync(hits, d_hits, total * sizeof(pm_hit),
+                                             cudaMemcpyDeviceToHost, st),
+                             "copy hits");
+        }
+    } else if (!rc && needed) {
+        rc = cuda_status(cudaMemcpyAsync(&total, d_offsets + npat, sizeof total,
+                                         cudaMemcpyDeviceToHost, st),
+                         "copy total");
+        waited = true;
+    }
+    cudaFreeAsync(scratch, st);
+    if (waited) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (!rc) rc = cuda_status(e, "stream synchronize");
+    }
+    if (rc) return rc;
+    if (waited) {
+        if (total == PM_TOTAL_ERROR) {
+            set_error("pm_search: a device wait timed out");
+            return PM_E_TIMEOUT;
+        }
+        if (needed) *needed = total;
+        if (total > capacity) {
+            set_error("pm_search: %llu hits, capacity %llu", (unsigned long long)total,
+                      (unsigned long long)capacity);
+            return PM_E_OVERFLOW;
+        }
+    }
+    return PM_OK;
+}
+
+pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                    const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                    uint64_t *needed, void *stream)
+{
+    return pm_search_ex(text, patterns, npat, k, hits, capacity, offsets, needed, nullptr, stream);
+}
+
+}  // extern "C"

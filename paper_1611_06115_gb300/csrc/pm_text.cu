@@ -1,0 +1,240 @@
+// Text coding (Sec. 2.1, Table 1) and the text handle.
+//
+// One thread codes one 32-symbol block: it reads 32 ASCII bytes (two 128-bit
+// loads when aligned) and produces the block's two bit planes.  Four bytes
+// are handled at once as one 32-bit word:
+//   code(x)  = ((x >> 1) ^ (x >> 2)) & 3 per byte gives A=0 C=1 G=2 T=3 for
+//              upper and lower case (bits 1-3 of the ASCII codes);
+//   validity = the byte with bit 5 cleared must equal the letter its code
+//              names, looked up with a byte permute; anything else is
+//              reported (the first offset wins, by atomicMin);
+//   packing  = the four low (high) code bits, one per byte, are gathered
+//              into four adjacent plane bits by one multiply, since the
+//              partial products of bits 0, 8, 16, 24 with 1 + 2^7 + 2^14 +
+//              2^21 land on distinct positions and those of interest are
+//              21..24.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+
+namespace {
+thread_local char g_err[512] = "";
+constexpr uint64_t kHostChunk = 256ull << 20;  // symbols per staged host piece
+
+__device__ __forceinline__ void code_word(uint32_t x, uint32_t &lo4, uint32_t &hi4, bool &ok)
+{
+    const uint32_t c = ((x >> 1) ^ (x >> 2)) & 0x03030303u;
+    const uint32_t t = c | (c >> 4);
+    const uint32_t selector = (t & 0xffu) | ((t >> 8) & 0xff00u);
+    const uint32_t canon = __byte_perm(0x54474341u, 0u, selector);  // "ACGT"
+    ok = (x & 0xdfdfdfdfu) == canon;
+    const uint32_t l = c & 0x01010101u;
+    const uint32_t h = (c >> 1) & 0x01010101u;
+    lo4 = ((l * 0x00204081u) >> 21) & 0xfu;
+    hi4 = ((h * 0x00204081u) >> 21) & 0xfu;
+}
+
+__global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t first,
+                       uint2 *__restrict__ planes, unsigned long long *__restrict__ bad, int aligned)
+{
+    const uint64_t nb = (n + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+        const uint64_t off = b * 32;
+        uint32_t w[8];
+        if (aligned && off + 32 <= n) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(ascii + off);
+            const uint4 u0 = __ldg(p), u1 = __ldg(p + 1);
+            w[0] = u0.x; w[1] = u0.y; w[2] = u0.z; w[3] = u0.w;
+            w[4] = u1.x; w[5] = u1.y; w[6] = u1.z; w[7] = u1.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint64_t s = off + 4 * q + i;
+                    const uint32_t ch = s < n ? (uint32_t)(uint8_t)ascii[s] : 0x41u;  // pad with A
+                    v |= ch << (8 * i);
+                }
+                w[q] = v;
+            }
+        }
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t l4, h4;
+            bool ok;
+            code_word(w[q], l4, h4, ok);
+            lo |= l4 << (4 * q);
+            hi |= h4 << (4 * q);
+            if (!ok) {
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t ch = (w[q] >> (8 * i)) & 0xffu;
+                    const uint32_t u = ch & 0xdfu;
+                    if (u != 'A' && u != 'C' && u != 'G' && u != 'T') {
+                        atomicMin(bad, (unsigned long long)(first + off + 4 * q + i));
+                        break;
+                    }
+                }
+            }
+        }
+        planes[first / 32 + b] = make_uint2(lo, hi);
+    }
+}
+
+}  // namespace
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+pm_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return PM_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PM_E_NOMEM : PM_E_CUDA;
+}
+
+bool is_device_pointer(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol, uint2 *planes,
+                        unsigned long long *bad, cudaStream_t stream)
+{
+    if (n_chunk == 0) return cudaSuccess;
+    const uint64_t nb = (n_chunk + 31) / 32;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (nb + 255) / 256;
+    const uint64_t cap = (uint64_t)sms * 16;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    const int aligned = ((uintptr_t)ascii % 16) == 0;
+    k_pack<<<grid, 256, 0, stream>>>(ascii, n_chunk, first_symbol, planes, bad, aligned);
+    return cudaGetLastError();
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+const char *pm_last_error(void) { return g_err; }
+
+const char *pm_status_string(pm_status s)
+{
+    switch (s) {
+    case PM_OK: return "ok";
+    case PM_E_ARG: return "invalid argument";
+    case PM_E_SYMBOL: return "text symbol outside A C G T";
+    case PM_E_NOMEM: return "out of memory";
+    case PM_E_OVERFLOW: return "more hits than capacity";
+    case PM_E_TOO_LARGE: return "size beyond the limits of this build";
+    case PM_E_TIMEOUT: return "a bounded device wait timed out";
+    case PM_E_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+    }
+}
+
+pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **out)
+{
+    if (!out || (!ascii && n > 0)) {
+        set_error("pm_encode_text: NULL argument");
+        return PM_E_ARG;
+    }
+    *out = nullptr;
+    if (n >= (1ull << 32)) {
+        set_error("pm_encode_text: n = %llu >= 2^32", (unsigned long long)n);
+        return PM_E_TOO_LARGE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pm_text *t = new (std::nothrow) pm_text{};
+    if (!t) return PM_E_NOMEM;
+    cudaGetDevice(&t->device);
+    t->n = n;
+    t->nblocks = (n + 31) / 32 + kPadBlocks;
+    pm_status rc = cuda_status(cudaMalloc(&t->planes, t->nblocks * sizeof(uint2)), "cudaMalloc planes");
+    if (rc) { delete t; return rc; }
+
+    unsigned long long *bad = nullptr;
+    char *staging = nullptr;
+    const bool on_device = is_device_pointer(ascii);
+    const uint64_t body = (n + 31) / 32;
+    rc = cuda_status(cudaMemsetAsync(t->planes + body, 0, (t->nblocks - body) * sizeof(uint2), st),
+                     "memset padding");
+    if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, sizeof *bad, st), "cudaMallocAsync");
+    if (!rc) rc = cuda_status(cudaMemsetAsync(bad, 0xff, sizeof *bad, st), "memset");
+    if (!rc && on_device) {
+        rc = cuda_status(launch_pack(ascii, n, 0, t->planes, bad, st), "pack kernel");
+    } else if (!rc && n > 0) {
+        const uint64_t chunk = n < kHostChunk ? n : kHostChunk;
+        rc = cuda_status(cudaMallocAsync((void **)&staging, (chunk + 15) & ~15ull, st),
+                         "cudaMallocAsync staging");
+        for (uint64_t off = 0; !rc && off < n; off += kHostChunk) {
+            const uint64_t len = n - off < kHostChunk ? n - off : kHostChunk;
+            rc = cuda_status(cudaMemcpyAsync(staging, ascii + off, len, cudaMemcpyHostToDevice, st),
+                             "copy text to device");
+            if (!rc) rc = cuda_status(launch_pack(staging, len, off, t->planes, bad, st), "pack kernel");
+        }
+    }
+    unsigned long long h_bad = ~0ull;
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st),
+                              "copy status");
+    if (staging) cudaFreeAsync(staging, st);
+    if (bad) cudaFreeAsync(bad, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc) rc = cuda_status(se, "stream synchronize");
+    if (!rc && h_bad != ~0ull) {
+        set_error("pm_encode_text: symbol at offset %llu is not A, C, G or T", h_bad);
+        rc = PM_E_SYMBOL;
+    }
+    if (rc) {
+        cudaFree(t->planes);
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return PM_OK;
+}
+
+uint64_t pm_text_length(const pm_text *text) { return text ? text->n : 0; }
+
+pm_status pm_text_device_planes(const pm_text *text, const void **planes, uint64_t *bytes)
+{
+    if (!text) return PM_E_ARG;
+    if (planes) *planes = text->planes;
+    if (bytes) *bytes = text->nblocks * sizeof(uint2);
+    return PM_OK;
+}
+
+void pm_text_free(pm_text *text)
+{
+    if (!text) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != text->device) cudaSetDevice(text->device);
+    cudaFree(text->planes);
+    if (cur != text->device) cudaSetDevice(cur);
+    delete text;
+}
+
+}  // extern "C"

@@ -64,6 +64,8 @@ def _clib() -> ctypes.CDLL:
             L = ctypes.CDLL(build())
             L.synth_markov.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_void_p, ctypes.c_int]
+            L.synth_markov_range.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
             L.synth_gc_fraction.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
             L.synth_gc_fraction.restype = ctypes.c_double
             _lib = L
@@ -131,16 +133,23 @@ def _thresholds(P: np.ndarray) -> np.ndarray:
     return np.clip(np.round(cum * 2.0 ** 32), 0, 2 ** 32 - 1).astype(np.uint32).reshape(-1)
 
 
+_THRESH: dict[float, np.ndarray] = {}
+
+
 def markov_text(n: int, seed: int, gc: float = 0.41, out: np.ndarray | None = None,
-                threads: int = 0) -> np.ndarray:
-    """Order-2 Markov ACGT text of length n (uint8 ASCII), written into ``out``
-    if given (any writable contiguous uint8 buffer, e.g. pinned host memory)."""
+                threads: int = 0, start: int = 0) -> np.ndarray:
+    """Symbols [start, start + n) of the order-2 Markov ACGT text with this seed
+    (uint8 ASCII), written into ``out`` if given (any writable contiguous uint8
+    buffer, e.g. pinned host memory).  Any range of the same seed agrees with
+    the corresponding slice of the whole text."""
     if out is None:
         out = np.empty(n, dtype=np.uint8)
     assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size >= n
-    thr = np.ascontiguousarray(_thresholds(markov_table(gc)))
-    _clib().synth_markov(out.ctypes.data, n, seed, thr.ctypes.data,
-                         threads or (os.cpu_count() or 1))
+    if gc not in _THRESH:
+        _THRESH[gc] = np.ascontiguousarray(_thresholds(markov_table(gc)))
+    thr = _THRESH[gc]
+    _clib().synth_markov_range(out.ctypes.data, start, n, seed, thr.ctypes.data,
+                               threads or (os.cpu_count() or 1))
     return out[:n]
 
 

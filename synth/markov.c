@@ -30,32 +30,34 @@ static inline uint64_t splitmix64(uint64_t x)
 
 typedef struct {
     uint8_t *out;
-    uint64_t n, seed;
+    uint64_t start, end, seed;
     const uint32_t *thr;
     uint64_t b0, b1;
 } job_t;
 
-static void gen_block(uint8_t *out, uint64_t n, uint64_t seed,
+/* Runs block b's chain and stores the symbols whose global index lies in
+ * [start, end) at out[index - start]. */
+static void gen_block(uint8_t *out, uint64_t start, uint64_t end, uint64_t seed,
                       const uint32_t *thr, uint64_t b)
 {
     static const uint8_t letters[4] = {'A', 'C', 'G', 'T'};
-    uint64_t start = b * (uint64_t)SYNTH_BLOCK;
-    uint64_t end = start + SYNTH_BLOCK;
-    if (end > n) end = n;
+    uint64_t i = b * (uint64_t)SYNTH_BLOCK;
+    uint64_t stop = i + SYNTH_BLOCK;
+    if (stop > end) stop = end;
     uint64_t key = splitmix64(seed ^ splitmix64(b + 0x5851f42d4c957f2dull));
     uint64_t ctr = 0;
     uint64_t r = splitmix64(key + ctr++);
     unsigned x2 = (unsigned)(r & 3), x1 = (unsigned)((r >> 2) & 3);
-    uint64_t i = start;
-    if (i < end) { out[i++] = letters[x2]; }
-    if (i < end) { out[i++] = letters[x1]; }
-    while (i < end) {
+    if (i < stop) { if (i >= start) out[i - start] = letters[x2]; ++i; }
+    if (i < stop) { if (i >= start) out[i - start] = letters[x1]; ++i; }
+    while (i < stop) {
         uint64_t w = splitmix64(key + ctr++);
-        for (int h = 0; h < 2 && i < end; ++h) {
+        for (int h = 0; h < 2 && i < stop; ++h) {
             uint32_t u = (uint32_t)(h ? (w >> 32) : w);
             const uint32_t *t = thr + 3 * (4 * x2 + x1);
             unsigned x = (u >= t[0]) + (u >= t[1]) + (u >= t[2]);
-            out[i++] = letters[x];
+            if (i >= start) out[i - start] = letters[x];
+            ++i;
             x2 = x1;
             x1 = x;
         }
@@ -65,27 +67,33 @@ static void gen_block(uint8_t *out, uint64_t n, uint64_t seed,
 static void *run(void *arg)
 {
     job_t *j = (job_t *)arg;
-    for (uint64_t b = j->b0; b < j->b1; ++b) gen_block(j->out, j->n, j->seed, j->thr, b);
+    for (uint64_t b = j->b0; b < j->b1; ++b)
+        gen_block(j->out, j->start, j->end, j->seed, j->thr, b);
     return NULL;
 }
 
-void synth_markov(uint8_t *out, uint64_t n, uint64_t seed,
-                  const uint32_t *thresholds, int nthreads)
+/* Symbols [start, start + len) of the text with the given seed. */
+void synth_markov_range(uint8_t *out, uint64_t start, uint64_t len, uint64_t seed,
+                        const uint32_t *thresholds, int nthreads)
 {
-    uint64_t nb = (n + SYNTH_BLOCK - 1) / SYNTH_BLOCK;
+    if (len == 0) return;
+    uint64_t end = start + len;
+    uint64_t bfirst = start / SYNTH_BLOCK, blast = (end - 1) / SYNTH_BLOCK + 1;
+    uint64_t nb = blast - bfirst;
     if (nthreads < 1) nthreads = 1;
-    if ((uint64_t)nthreads > nb) nthreads = nb ? (int)nb : 1;
+    if ((uint64_t)nthreads > nb) nthreads = (int)nb;
     job_t *jobs = (job_t *)calloc((size_t)nthreads, sizeof(job_t));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
     if (!jobs || !th) {
-        for (uint64_t b = 0; b < nb; ++b) gen_block(out, n, seed, thresholds, b);
+        for (uint64_t b = bfirst; b < blast; ++b) gen_block(out, start, end, seed, thresholds, b);
         free(jobs); free(th);
         return;
     }
     for (int q = 0; q < nthreads; ++q) {
-        jobs[q].out = out; jobs[q].n = n; jobs[q].seed = seed; jobs[q].thr = thresholds;
-        jobs[q].b0 = nb * (uint64_t)q / (uint64_t)nthreads;
-        jobs[q].b1 = nb * (uint64_t)(q + 1) / (uint64_t)nthreads;
+        jobs[q].out = out; jobs[q].start = start; jobs[q].end = end;
+        jobs[q].seed = seed; jobs[q].thr = thresholds;
+        jobs[q].b0 = bfirst + nb * (uint64_t)q / (uint64_t)nthreads;
+        jobs[q].b1 = bfirst + nb * (uint64_t)(q + 1) / (uint64_t)nthreads;
     }
     int started = 0;
     for (int q = 1; q < nthreads; ++q) {
@@ -96,6 +104,12 @@ void synth_markov(uint8_t *out, uint64_t n, uint64_t seed,
     for (int q = started + 1; q < nthreads; ++q) run(&jobs[q]);
     for (int q = 1; q <= started; ++q) pthread_join(th[q], NULL);
     free(jobs); free(th);
+}
+
+void synth_markov(uint8_t *out, uint64_t n, uint64_t seed,
+                  const uint32_t *thresholds, int nthreads)
+{
+    synth_markov_range(out, 0, n, seed, thresholds, nthreads);
 }
 
 /* GC fraction of a text (counts C and G), for calibration checks. */

@@ -15,6 +15,12 @@ def test_markov_reproducible_across_thread_counts():
     assert set(np.unique(a).tolist()) <= set(b"ACGT")
 
 
+def test_markov_range_is_a_slice():
+    full = synth.markov_text(5_000_000, seed=2)
+    for a, b in ((0, 10), (1_048_570, 1_048_600), (123_456, 3_210_000), (4_999_000, 5_000_000)):
+        assert np.array_equal(synth.markov_text(b - a, seed=2, start=a), full[a:b])
+
+
 def test_markov_gc_and_cpg():
     t = synth.markov_text(20_000_000, seed=3)
     assert abs(synth.gc_fraction(t) - 0.41) < 0.002
