@@ -289,7 +289,7 @@ def run_ours(a):
     # ---- e2e through the public API with host buffers ----
     e2e_times = []
     h2d = d2h = 0
-    for it in range(a.e2e_steps + 1):
+    for it in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tx = pm.pm_encode_text(host, stream=stream)
@@ -304,12 +304,12 @@ def run_ours(a):
         h2d = n_local + sum(16 * ((len(p) + 31) // 32) for p in pats) + 16 * len(ents)
         d2h = 8 * tot + 8 * (len(ents) + 1)
         del tx, rr
-    e2e_s = statistics.median(e2e_times)
+    e2e_s = statistics.median(e2e_times) if e2e_times else float("nan")
     if world > 1:
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    e2e_value = world * cells(n, ents) / e2e_s
+    e2e_value = world * cells(n, ents) / e2e_s if e2e_times else None
 
     line = {
         "metric": METRIC,
@@ -352,7 +352,7 @@ def run_ours(a):
         "setup_s": {"generate": gen_s, "encode": encode_s,
                     "encode_gbs": n_local / encode_s / 1e9},
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and a.cpu_seconds > 0:
         S, t, v = oracle_sample(n, pats, a.cpu_seconds, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": v, "unit": "window-cells/s", "cores": os.cpu_count(),
                                 "kind": "oracle",
