@@ -186,6 +186,42 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                        const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
                        uint64_t *needed, const pm_options *options, void *stream);
 
+/*
+ * pm_search_noalloc -- pm_search for callers that must not allocate memory.
+ * The paper has no counterpart: this is a deployment concern, not part of
+ * the method.
+ *
+ * Who needs it: code that runs where calling the CUDA allocator is not
+ * allowed or not wanted, for example inside a host callback, in a
+ * real-time loop that may not take the allocator's locks or its implicit
+ * synchronisation, or in an application that has already handed all of
+ * its device memory to its own allocator.  pm_search draws its scratch from
+ * the stream-ordered pool and a pinned host ring; this entry point draws it
+ * from one fixed array (about 57 MiB) that the library declares in device
+ * global memory.  Every GPU that loads the library holds that array until
+ * the process exits.  The call performs no cudaMalloc, cudaMallocAsync,
+ * cudaHostAlloc or free of any kind.
+ *
+ * Arguments are those of pm_search, except that hits and offsets must be
+ * device memory (PM_E_ARG otherwise).  Results are identical to pm_search's.
+ *
+ * Limits (PM_E_TOO_LARGE beyond them, nothing queued): at most 64 (pattern,
+ * k) pairs, at most 4096 32-position chunks over the distinct patterns
+ * (e.g. m up to 131072 for one pattern), at most 2^20 tiles of 8192 windows
+ * over all pairs (e.g. 8.5e9 windows for one pattern), capacity at most
+ * 2^22 hits.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (the call clears what has to start at zero):
+ * calls whose work overlaps on the GPU, such as calls on two streams or from
+ * two threads, race with each other.  Issue them on one stream.
+ */
+pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patterns,
+                            uint32_t npat, const int32_t *k, pm_hit *hits, uint64_t capacity,
+                            uint64_t *offsets, uint64_t *needed, void *stream);
+
 /* ---------------------------------------------------------------- status */
 
 const char *pm_status_string(pm_status status);

@@ -64,6 +64,8 @@ SIGNATURES = {
                          ctypes.POINTER(_u64), _vp]),
     "pm_search_ex": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _vp, _u64, _vp,
                             ctypes.POINTER(_u64), ctypes.POINTER(pm_options), _vp]),
+    "pm_search_noalloc": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _vp, _u64,
+                                 _vp, ctypes.POINTER(_u64), _vp]),
     "pm_status_string": (ctypes.c_char_p, [_i32]),
     "pm_last_error": (ctypes.c_char_p, []),
 }

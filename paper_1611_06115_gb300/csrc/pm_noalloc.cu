@@ -1,0 +1,205 @@
+// pm_search_noalloc: the search without any memory allocation.
+//
+// Some callers cannot allocate device memory during a search: code running
+// inside a host callback or a driver thread that must not call into the
+// allocator, applications whose device memory is fully carved up by their own
+// allocator before the search starts, and real-time loops where an
+// allocation (and the implicit synchronisation it may cause) is not allowed.
+// pm_search takes its scratch from the stream-ordered pool and a pinned host
+// ring, so it does not suit them.  This entry point runs the same scan and
+// ordering kernels, but every byte of scratch lives in one fixed array in
+// device global memory that the library declares at file scope.  The array
+// is part of the module: each GPU that loads libpm keeps it until the
+// process exits.  Calls allocate nothing (no cudaMalloc, cudaMallocAsync,
+// cudaHostAlloc or free).
+//
+// Because every call uses the same array, two calls whose work overlaps on
+// the GPU (different streams, or different host threads) race and corrupt
+// each other's results; serialise them, e.g. by issuing them on one stream.
+#include <mutex>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+// Limits of this entry point (checked on every call).
+constexpr uint32_t kNaMaxPatterns = 64;            // (pattern, k) pairs per call
+constexpr uint64_t kNaMaxChunks = 4096;            // sum of ceil(m/32) over distinct patterns
+constexpr uint64_t kNaMaxTiles = 1ull << 20;       // sum of ceil((n-m+1)/8192) over the pairs
+constexpr uint64_t kNaMaxHits = 1ull << 22;        // capacity
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kOffMasks = 0;
+constexpr size_t kOffTile0 = kOffMasks + al256(kNaMaxChunks * sizeof(uint4));
+constexpr size_t kOffCtl = kOffTile0 + al256((kNaMaxPatterns + 1) * sizeof(uint64_t));
+constexpr size_t kOffTable = kOffCtl + 256;
+constexpr size_t kOffTmp = kOffTable + al256(kNaMaxTiles * sizeof(TileEntry));
+constexpr size_t kOffOrder = kOffTmp + al256(kNaMaxHits * sizeof(pm_hit));
+// order scratch: per-block partials (+1) and one destination per tile entry
+constexpr size_t kOrderBytes = (kNaMaxTiles / 4096 + 2) * 8 + kNaMaxTiles * 8 + 256;
+constexpr size_t kScratchBytes = kOffOrder + al256(kOrderBytes);
+
+// The scratch array (about 57 MiB).  Host code must not use its name as an
+// address: the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDev];
+
+// Once per device, with that device current: look up the array's address.
+pm_status scratch_address(int dev, char **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_status(e != cudaSuccess ? e : cudaErrorUnknown,
+                                                        "cudaGetSymbolAddress(scratch)");
+        g_addr[dev] = p;
+    }
+    *out = (char *)g_addr[dev];
+    return PM_OK;
+}
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                            const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                            uint64_t *needed, void *stream)
+{
+    if (!text || !offsets || (npat > 0 && (!patterns || !k)) || (capacity > 0 && !hits)) {
+        set_error("pm_search_noalloc: NULL argument");
+        return PM_E_ARG;
+    }
+    if (npat > kNaMaxPatterns) {
+        set_error("pm_search_noalloc: npat = %u exceeds this entry point's limit of %u", npat,
+                  kNaMaxPatterns);
+        return PM_E_TOO_LARGE;
+    }
+    if (capacity > kNaMaxHits) {
+        set_error("pm_search_noalloc: capacity %llu exceeds this entry point's limit of %llu hits",
+                  (unsigned long long)capacity, (unsigned long long)kNaMaxHits);
+        return PM_E_TOO_LARGE;
+    }
+    for (uint32_t p = 0; p < npat; ++p) {
+        if (!patterns[p] || k[p] < 0) {
+            set_error("pm_search_noalloc: pattern %u is NULL or has k < 0", p);
+            return PM_E_ARG;
+        }
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDev || dev != text->device) {
+        set_error("pm_search_noalloc: text lives on device %d, current device is %d", text->device,
+                  dev);
+        return PM_E_ARG;
+    }
+    if (!is_device_pointer(offsets) || (capacity > 0 && !is_device_pointer(hits))) {
+        set_error("pm_search_noalloc: hits and offsets must be device memory");
+        return PM_E_ARG;
+    }
+
+    // descriptors; a handle repeated with several k is packed once
+    PatDesc desc[kNaMaxPatterns];
+    uint64_t tile0[kNaMaxPatterns + 1];
+    const pm_pattern *distinct[kNaMaxPatterns];
+    uint64_t where[kNaMaxPatterns];
+    uint32_t ndistinct = 0;
+    uint64_t nmask = 0, entries = 0;
+    for (uint32_t p = 0; p < npat; ++p) {
+        const pm_pattern *pt = patterns[p];
+        uint64_t mo = ~0ull;
+        for (uint32_t q = 0; q < ndistinct; ++q)
+            if (distinct[q] == pt) mo = where[q];
+        if (mo == ~0ull) {
+            mo = nmask;
+            distinct[ndistinct] = pt;
+            where[ndistinct++] = mo;
+            nmask += pt->nchunks;
+        }
+        PatDesc &d = desc[p];
+        d.m = pt->m;
+        d.nchunks = pt->nchunks;
+        d.k = k[p];
+        d.pad0 = 0;
+        d.masks = mo;
+        d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
+        d.tile0 = entries;
+        d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
+        entries += d.ntiles;
+        tile0[p] = d.tile0;
+    }
+    tile0[npat] = entries;
+    if (nmask > kNaMaxChunks || entries > kNaMaxTiles) {
+        set_error("pm_search_noalloc: %llu pattern chunks (limit %llu) and %llu tiles (limit %llu)",
+                  (unsigned long long)nmask, (unsigned long long)kNaMaxChunks,
+                  (unsigned long long)entries, (unsigned long long)kNaMaxTiles);
+        return PM_E_TOO_LARGE;
+    }
+
+    char *base = nullptr;
+    pm_status rc = scratch_address(dev, &base);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint4 *d_masks = (uint4 *)(base + kOffMasks);
+    uint64_t *d_tile0 = (uint64_t *)(base + kOffTile0);
+    char *ctl = base + kOffCtl;
+    unsigned long long *d_cursor = (unsigned long long *)ctl;
+    uint32_t *d_status = (uint32_t *)(ctl + 8);
+    TileEntry *d_table = (TileEntry *)(base + kOffTable);
+    pm_hit *d_tmp = (pm_hit *)(base + kOffTmp);
+    void *d_order = base + kOffOrder;
+
+    // Copies from pageable host memory are staged by the driver: the source
+    // may be reused as soon as each call returns.
+    for (uint32_t q = 0; !rc && q < ndistinct; ++q)
+        rc = cuda_status(cudaMemcpyAsync(d_masks + where[q], distinct[q]->masks,
+                                         distinct[q]->nchunks * sizeof(uint4),
+                                         cudaMemcpyHostToDevice, st),
+                         "upload masks");
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(d_tile0, tile0, (npat + 1) * sizeof(uint64_t),
+                                         cudaMemcpyHostToDevice, st),
+                         "upload tile offsets");
+    // the array keeps the previous call's contents: the hit cursor and the
+    // status word must start at zero (the tile table is rewritten in full)
+    if (!rc) rc = cuda_status(cudaMemsetAsync(ctl, 0, 256, st), "clear control words");
+    for (uint32_t p = 0; !rc && p < npat; ++p) {
+        const Variant v = ws_bits(desc[p].k) >= 0 && ws_bits(desc[p].k) <= 2 ? Variant::kWindowSliced
+                                                                             : Variant::kPatternSliced;
+        rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
+                                     d_cursor, d_status, scan_grid_limit(v, dev), st),
+                         "scan kernel");
+    }
+    if (!rc)
+        rc = cuda_status(launch_order(d_table, entries, d_tile0, npat, d_tmp, hits, capacity, offsets,
+                                      d_status, d_order, st),
+                         "order kernels");
+    if (rc || !needed) return rc;
+    uint64_t total = 0;
+    rc = cuda_status(cudaMemcpyAsync(&total, offsets + npat, sizeof total, cudaMemcpyDeviceToHost, st),
+                     "copy total");
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
+    if (rc) return rc;
+    if (total == PM_TOTAL_ERROR) {
+        set_error("pm_search_noalloc: a device wait timed out");
+        return PM_E_TIMEOUT;
+    }
+    *needed = total;
+    if (total > capacity) {
+        set_error("pm_search_noalloc: %llu hits, capacity %llu", (unsigned long long)total,
+                  (unsigned long long)capacity);
+        return PM_E_OVERFLOW;
+    }
+    return PM_OK;
+}
+
+}  // extern "C"
