@@ -133,7 +133,7 @@ void pm_pattern_free(pm_pattern *pattern);
  * npat      number of patterns, 0 <= npat <= PM_MAX_BATCH.
  * k         host array of npat values, each >= 0.
  * hits      output, capacity records, host or device.
- * capacity  number of records hits can hold.
+ * capacity  number of records hits can hold, at most 2^32 - 1.
  * offsets   output, npat+1 values, host or device (same kind as hits).
  *           Pattern p's hits are hits[offsets[p] .. offsets[p+1]), sorted
  *           by location; offsets[npat] is the total.
@@ -197,7 +197,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
  * synchronisation, or in an application that has already handed all of
  * its device memory to its own allocator.  pm_search draws its scratch from
  * the stream-ordered pool and a pinned host ring; this entry point draws it
- * from one fixed array (about 57 MiB) that the library declares in device
+ * from one fixed array (about 64 MiB) that the library declares in device
  * global memory.  Every GPU that loads the library holds that array until
  * the process exits.  The call performs no cudaMalloc, cudaMallocAsync,
  * cudaHostAlloc or free of any kind.
@@ -207,8 +207,8 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
  *
  * Limits (PM_E_TOO_LARGE beyond them, nothing queued): at most 64 (pattern,
  * k) pairs, at most 4096 32-position chunks over the distinct patterns
- * (e.g. m up to 131072 for one pattern), at most 2^20 tiles of 8192 windows
- * over all pairs (e.g. 8.5e9 windows for one pattern), capacity at most
+ * (e.g. m up to 131072 for one pattern), at most 2^21 tiles of 4096 windows
+ * over all pairs (e.g. 8.6e9 windows for one pattern), capacity at most
  * 2^22 hits.
  *
  * Set-up: the first call on a device looks up the array's device address

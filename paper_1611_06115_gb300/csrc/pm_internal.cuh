@@ -31,38 +31,53 @@ struct pm_pattern {
     uint32_t nchunks;
     uint32_t unknown;  // symbols coded "-" because Table 2 does not list them
     uint4 *masks;      // host, nchunks entries
+    // The first min(m, 32) positions as a list for the window-sliced scan:
+    // n_single entries {shift j, X, Y, 0} for one-letter classes (X, Y the
+    // letter's code bits broadcast to whole words), then n_general pairs
+    // {j, 0, 0, 0}, {A, C, G, T} (membership broadcast) for the other
+    // classes; N (every letter) is left out because it never mismatches.
+    uint32_t n_single;
+    uint32_t n_general;
+    uint4 *wslist;     // host, n_single + 2 * n_general entries
 };
 
 namespace pm {
 
 constexpr int kScanThreads = 256;                        // threads per scan CTA
-constexpr uint64_t kTileBlocks = kScanThreads;           // one block per thread
-constexpr uint64_t kTileWindows = 32ull * kTileBlocks;   // windows per tile
-constexpr int kHaloBlocks = 2;                           // staged after the tile
-constexpr uint32_t kTileBytes = (uint32_t)((kTileBlocks + kHaloBlocks) * sizeof(uint2));
+constexpr int kScanWarps = kScanThreads / 32;
+constexpr int kGroups = 4;                               // 32-window groups per lane per tile
+constexpr uint64_t kTileWindows = 32ull * 32 * kGroups;  // one warp tile: 4096 windows
+constexpr int kStageBlocks = 32 * kGroups + 2;           // a warp tile's blocks + 2 halo blocks
+constexpr uint32_t kStageBytes = kStageBlocks * 8;       // one bulk copy per warp tile
 constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
 constexpr uint64_t kWaitLimitNs = 1000000000ull;         // bounded device waits: 1 s
+constexpr int kWsMaxK = 6;                               // window-sliced scan handles k <= 6
+constexpr uint64_t kMaxCapacity = 0xffffffffull;         // hits addressable by a tile entry
 
-static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+static_assert(kStageBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
-// One pattern of a search, as the kernels see it.
+// One (pattern, k) of a search, as the kernels see it.
 struct PatDesc {
-    uint32_t m;        // pattern length
-    uint32_t nchunks;  // ceil(m / 32)
-    int32_t k;         // allowed mismatches (>= 0)
+    uint32_t m;          // pattern length
+    uint32_t nchunks;    // ceil(m / 32)
+    int32_t k;           // allowed mismatches (>= 0)
+    uint32_t n_single;   // window-sliced list: one-letter entries
+    uint32_t n_general;  // window-sliced list: other-class entry pairs
+    uint32_t two;        // 2 and 2^27, given at run time so that the multiply-adds
+    uint32_t c27;        //   built on them stay multiply-adds (FMA pipe)
     uint32_t pad0;
-    uint64_t masks;    // index of chunk 0 in the mask arena (uint4 units)
-    uint64_t nwin;     // windows: n - m + 1, or 0 when m > n
-    uint64_t tile0;    // first tile-table entry of this pattern
-    uint64_t ntiles;   // ceil(nwin / kTileWindows)
+    uint64_t masks;      // chunk 0 in the arena (uint4 units)
+    uint64_t wslist;     // window-sliced list in the arena (uint4 units)
+    uint64_t nwin;       // windows: n - m + 1, or 0 when m > n
+    uint64_t tile0;      // first tile-table entry of this pattern
+    uint64_t ntiles;     // ceil(nwin / kTileWindows)
 };
 
-// Hits of one (pattern, tile): where the scan kernel put them in the
-// scratch hit buffer, and how many.  Within a tile they are in window order.
+// Hits of one (pattern, warp tile): how many, and where the scan kernel put
+// them in the scratch hit buffer.  Within a tile they are in window order.
 struct TileEntry {
-    unsigned long long src;
     uint32_t count;
-    uint32_t pad0;
+    uint32_t src;
 };
 
 // Device status bits written by kernels.
@@ -71,19 +86,27 @@ constexpr uint32_t kDevTimeout = 1u;
 // Scan-kernel variants.
 enum class Variant : int {
     kPatternSliced = 0,  // per window, 32 positions per word, popc
-    kWindowSliced = 1,   // per position, 32 windows per word, bit-sliced counter
+    kWindowSliced = 1,   // per position, 32 windows per word, thermometer counter (k <= 6)
 };
 
 // Launch one scan kernel for one pattern (pm_scan.cu).
-cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *masks,
+cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *arena,
                         TileEntry *table, pm_hit *tmp, uint64_t cap, unsigned long long *cursor,
                         uint32_t *status, int grid, cudaStream_t stream);
 
 // Number of resident scan CTAs the device runs at once (pm_scan.cu).
-int scan_grid_limit(Variant v, int device);
+int scan_grid_limit(Variant v, int32_t k, int device);
 
-// Window-sliced counter width for k, or -1 if k is too large for it.
-int ws_bits(int32_t k);
+// The variant chosen when the caller leaves it open.
+Variant auto_variant(const PatDesc &d);
+
+// Fill the run-time constants of a descriptor.
+inline void desc_constants(PatDesc &d)
+{
+    d.two = 2u;
+    d.c27 = 1u << 27;
+    d.pad0 = 0u;
+}
 
 // Ordering: exclusive scan of table counts, per-pattern CSR offsets, and the
 // gather of hits into their final places (pm_order.cu).  Needs

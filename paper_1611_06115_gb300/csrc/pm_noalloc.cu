@@ -27,12 +27,14 @@ namespace {
 // Limits of this entry point (checked on every call).
 constexpr uint32_t kNaMaxPatterns = 64;            // (pattern, k) pairs per call
 constexpr uint64_t kNaMaxChunks = 4096;            // sum of ceil(m/32) over distinct patterns
-constexpr uint64_t kNaMaxTiles = 1ull << 20;       // sum of ceil((n-m+1)/8192) over the pairs
+constexpr uint64_t kNaMaxTiles = 1ull << 21;       // sum of ceil((n-m+1)/4096) over the pairs
 constexpr uint64_t kNaMaxHits = 1ull << 22;        // capacity
+// arena: chunk masks plus each distinct pattern's window-sliced list (<= 64 entries)
+constexpr uint64_t kNaMaxArena = kNaMaxChunks + 64ull * kNaMaxPatterns;
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffMasks = 0;
-constexpr size_t kOffTile0 = kOffMasks + al256(kNaMaxChunks * sizeof(uint4));
+constexpr size_t kOffTile0 = kOffMasks + al256(kNaMaxArena * sizeof(uint4));
 constexpr size_t kOffCtl = kOffTile0 + al256((kNaMaxPatterns + 1) * sizeof(uint64_t));
 constexpr size_t kOffTable = kOffCtl + 256;
 constexpr size_t kOffTmp = kOffTable + al256(kNaMaxTiles * sizeof(TileEntry));
@@ -41,7 +43,7 @@ constexpr size_t kOffOrder = kOffTmp + al256(kNaMaxHits * sizeof(pm_hit));
 constexpr size_t kOrderBytes = (kNaMaxTiles / 4096 + 2) * 8 + kNaMaxTiles * 8 + 256;
 constexpr size_t kScratchBytes = kOffOrder + al256(kOrderBytes);
 
-// The scratch array (about 57 MiB).  Host code must not use its name as an
+// The scratch array (about 64 MiB).  Host code must not use its name as an
 // address: the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -123,14 +125,17 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
             mo = nmask;
             distinct[ndistinct] = pt;
             where[ndistinct++] = mo;
-            nmask += pt->nchunks;
+            nmask += pt->nchunks + pt->n_single + 2ull * pt->n_general;
         }
         PatDesc &d = desc[p];
         d.m = pt->m;
         d.nchunks = pt->nchunks;
         d.k = k[p];
-        d.pad0 = 0;
+        d.n_single = pt->n_single;
+        d.n_general = pt->n_general;
+        desc_constants(d);
         d.masks = mo;
+        d.wslist = mo + pt->nchunks;
         d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
         d.tile0 = entries;
         d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
@@ -138,9 +143,11 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
         tile0[p] = d.tile0;
     }
     tile0[npat] = entries;
-    if (nmask > kNaMaxChunks || entries > kNaMaxTiles) {
+    uint64_t chunks = 0;
+    for (uint32_t q = 0; q < ndistinct; ++q) chunks += distinct[q]->nchunks;
+    if (chunks > kNaMaxChunks || entries > kNaMaxTiles) {
         set_error("pm_search_noalloc: %llu pattern chunks (limit %llu) and %llu tiles (limit %llu)",
-                  (unsigned long long)nmask, (unsigned long long)kNaMaxChunks,
+                  (unsigned long long)chunks, (unsigned long long)kNaMaxChunks,
                   (unsigned long long)entries, (unsigned long long)kNaMaxTiles);
         return PM_E_TOO_LARGE;
     }
@@ -160,11 +167,17 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
 
     // Copies from pageable host memory are staged by the driver: the source
     // may be reused as soon as each call returns.
-    for (uint32_t q = 0; !rc && q < ndistinct; ++q)
-        rc = cuda_status(cudaMemcpyAsync(d_masks + where[q], distinct[q]->masks,
-                                         distinct[q]->nchunks * sizeof(uint4),
+    for (uint32_t q = 0; !rc && q < ndistinct; ++q) {
+        const pm_pattern *pt = distinct[q];
+        rc = cuda_status(cudaMemcpyAsync(d_masks + where[q], pt->masks, pt->nchunks * sizeof(uint4),
                                          cudaMemcpyHostToDevice, st),
                          "upload masks");
+        const uint64_t nl = pt->n_single + 2ull * pt->n_general;
+        if (!rc && nl)
+            rc = cuda_status(cudaMemcpyAsync(d_masks + where[q] + pt->nchunks, pt->wslist,
+                                             nl * sizeof(uint4), cudaMemcpyHostToDevice, st),
+                             "upload lists");
+    }
     if (!rc)
         rc = cuda_status(cudaMemcpyAsync(d_tile0, tile0, (npat + 1) * sizeof(uint64_t),
                                          cudaMemcpyHostToDevice, st),
@@ -173,10 +186,9 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
     // status word must start at zero (the tile table is rewritten in full)
     if (!rc) rc = cuda_status(cudaMemsetAsync(ctl, 0, 256, st), "clear control words");
     for (uint32_t p = 0; !rc && p < npat; ++p) {
-        const Variant v = ws_bits(desc[p].k) >= 0 && ws_bits(desc[p].k) <= 2 ? Variant::kWindowSliced
-                                                                             : Variant::kPatternSliced;
+        const Variant v = auto_variant(desc[p]);
         rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
-                                     d_cursor, d_status, scan_grid_limit(v, dev), st),
+                                     d_cursor, d_status, scan_grid_limit(v, desc[p].k, dev), st),
                          "scan kernel");
     }
     if (!rc)

@@ -131,6 +131,30 @@ pm_status pm_compile_pattern(const char *iupac, uint32_t m, pm_pattern **out)
         uint4 &w = p->masks[j >> 5];
         w.x |= bit; w.y |= bit; w.z |= bit; w.w |= bit;
     }
+    // window-sliced position list (first 32 positions)
+    const uint32_t head = m < 32 ? m : 32;
+    p->wslist = new (std::nothrow) uint4[2 * head + 1];
+    if (!p->wslist) {
+        delete[] p->masks;
+        delete p;
+        return PM_E_NOMEM;
+    }
+    // one-letter classes first (the most selective), each as its code bits
+    for (uint32_t j = 0; j < head; ++j) {
+        const uint8_t mask = tab.mask[(unsigned char)iupac[j]];
+        if (__builtin_popcount(mask) != 1) continue;
+        const uint32_t code = (uint32_t)__builtin_ctz(mask);  // A=0 C=1 G=2 T=3
+        p->wslist[p->n_single++] = make_uint4(j, 0u - (code & 1u), 0u - (code >> 1), 0u);
+    }
+    // then the other classes except N (which never mismatches), as membership words
+    for (uint32_t j = 0; j < head; ++j) {
+        const uint8_t mask = tab.mask[(unsigned char)iupac[j]];
+        if (mask == 0xf || __builtin_popcount(mask) == 1) continue;
+        uint4 *e = p->wslist + p->n_single + 2 * p->n_general++;
+        e[0] = make_uint4(j, 0u, 0u, 0u);
+        e[1] = make_uint4(0u - (mask & 1u), 0u - ((mask >> 1) & 1u), 0u - ((mask >> 2) & 1u),
+                          0u - ((mask >> 3) & 1u));
+    }
     *out = p;
     return PM_OK;
 }
@@ -152,6 +176,7 @@ void pm_pattern_free(pm_pattern *p)
 {
     if (!p) return;
     delete[] p->masks;
+    delete[] p->wslist;
     delete p;
 }
 

@@ -1,32 +1,38 @@
-// Scan kernels: Eq. 4 with the early stop of Sec. 2.4-2.5 over one tile of
-// the text after another (Sec. 2.6).
+// Scan kernels: Eq. 4 with the early stop of Sec. 2.4-2.5 over warp tiles of
+// the text (Sec. 2.6).
 //
-// A tile is kTileBlocks consecutive 32-symbol blocks; thread t of the CTA
-// owns the 32 windows that start in block t of the tile.  Every window of a
-// tile needs at most m-1 symbols beyond it (the overlap of Sec. 2.6): the
-// first two blocks (tile + one halo block) come from shared memory, filled by
-// a bulk (TMA) copy that runs one tile ahead; deeper blocks, which only the
-// rare windows still alive after 32 positions read, come through L1/L2.
+// Work unit: a warp tile of kGroups x 32 consecutive 32-symbol blocks.  Lane l
+// owns the 32 windows that start in block 32g + l of the tile, for each group
+// g.  Windows need at most m-1 symbols beyond their tile (the overlap of
+// Sec. 2.6): the tile and a 2-block halo arrive in shared memory by one bulk
+// (TMA) copy, issued by the warp itself two tiles ahead into a two-stage
+// ring with one mbarrier per stage; deeper blocks, read only by the rare
+// windows still alive after 32 positions, come through L1/L2.  Warps never
+// wait for each other: each persistent warp walks its own tiles, and a
+// tile's hits are emitted by a warp-aggregated atomic.
 //
-// Two ways to evaluate the sum for the first 32 positions:
+// The first 32 positions are evaluated in one of two ways.
 //
-//  * pattern-sliced: for each window, one 32-bit word holds the 32 text
-//    symbols under the first 32 pattern positions (two funnel shifts of the
-//    bit planes), Table 3 is applied to all 32 pairs with three bitwise
-//    selects, and __popc gives the mismatch count;
-//  * window-sliced: for each pattern position j, one word holds the 32
-//    windows' text symbols at offset j, the class test gives a 32-window
-//    mismatch word, and a bit-sliced counter adds it to 32 running sums at
-//    once.  The counter starts at 2^B - (k+1), so a carry out of its top bit
-//    marks the windows whose sum exceeded k; the thread stops as soon as all
-//    of its 32 windows are out (early stop of Sec. 2.4).
+//  * pattern-sliced (any k): per window, one 32-bit word holds the text
+//    symbols under positions 0..31 (two funnel shifts of the bit planes);
+//    three bitwise selects apply Table 3 to all 32 pairs; __popc counts the
+//    matches g.  Four windows' g are packed into the bytes of one word by
+//    multiply-adds (FMA pipe) together with k in every byte; bit 5 of a byte
+//    is then set exactly when g + k >= 32, i.e. when the window has at most
+//    k mismatches, and two ALU steps move those four bits into the lane's
+//    pass mask (in a transposed bit order, undone only when a window passes).
+//  * window-sliced (k <= 6): per pattern position j, one word holds the 32
+//    windows' symbols at offset j; a one-letter class gives the mismatch word
+//    in two XOR/OR steps, other classes in three selects, N in none; a
+//    thermometer counter of k+1 words (level i set once a window has more
+//    than i mismatches) adds 32 windows' mismatches at once.  The positions
+//    come from a list built by pm_compile_pattern; each list entry read
+//    from shared memory serves all groups, and the warp stops as soon as
+//    every window of the tile is past k (the early stop of Sec. 2.4).
 //
-// Windows still at or below k after 32 positions continue one at a time,
-// 32 positions per step, stopping once their sum exceeds k.  Hits of a tile
-// are written in window order: a CTA-wide prefix sum of per-thread hit
-// counts, one atomicAdd per tile to reserve room in the scratch hit buffer,
-// and a tile-table entry recording where they went (pm_order.cu puts the
-// tiles in order).
+// Windows still at or below k after those 32 positions are counted again one
+// at a time, 32 positions per step, from position 0 until their sum exceeds k
+// or the pattern ends; that count is exact and is what a hit reports.
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -34,7 +40,10 @@ namespace {
 
 using dev::class_match;
 
-// Mismatch count of window 32*blk + w from chunk c0 on, starting from
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int G = kGroups;
+
+// Mismatch count of window 32*blk + w over chunks c0.., starting from
 // `count`, stopping once it exceeds `limit` (then some value > limit).
 __device__ __forceinline__ uint32_t window_count_from(const uint2 *__restrict__ planes,
                                                       uint64_t blk, uint32_t w,
@@ -54,196 +63,292 @@ __device__ __forceinline__ uint32_t window_count_from(const uint2 *__restrict__ 
     return count;
 }
 
-// Windows of this thread that pass: bit w for window 32*blk + w.
-// Pattern-sliced evaluation of the first chunk.
-__device__ __forceinline__ uint32_t survivors_pattern_sliced(uint2 a, uint2 b, uint4 M0, uint32_t k)
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// The pass masks below use a transposed bit order: window 4j + b of the lane
+// sits at bit 8b + j.  This restores the natural order (window w at bit w).
+__device__ __forceinline__ uint32_t untranspose(uint32_t t)
+{
+    uint32_t r = 0;
+    while (t) {
+        const uint32_t p = __ffs(t) - 1;
+        t &= t - 1;
+        r |= 1u << (4 * (p & 7) + (p >> 3));
+    }
+    return r;
+}
+
+// Pattern-sliced first chunk for one lane's 32 windows; transposed pass mask
+// of the windows with at most k mismatches in positions 0..31 (k <= 31).
+// k4 = k in every byte; one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
+__device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint4 M0, uint32_t k4,
+                                                        uint32_t one, uint32_t m8, uint32_t m16,
+                                                        uint32_t m24)
 {
     uint32_t pass = 0;
 #pragma unroll
-    for (int w = 0; w < 32; ++w) {
-        const uint32_t lo = __funnelshift_r(a.x, b.x, w);
-        const uint32_t hi = __funnelshift_r(a.y, b.y, w);
-        const uint32_t c = __popc(~class_match(lo, hi, M0));
-        pass |= (c <= k ? 1u : 0u) << w;
+    for (int j = 0; j < 8; ++j) {
+        uint32_t g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = 4 * j + q;
+            const uint32_t lo = __funnelshift_r(a.x, b.x, w);
+            const uint32_t hi = __funnelshift_r(a.y, b.y, w);
+            g[q] = __popc(class_match(lo, hi, M0));
+        }
+        uint32_t v = mad_lo(g[3], m24, k4);
+        v = mad_lo(g[2], m16, v);
+        v = mad_lo(g[1], m8, v);
+        v = mad_lo(g[0], one, v);
+        // bit 5 of byte q: g[q] + k >= 32; move bits 5, 13, 21, 29 to 8q + j
+        const uint32_t s = j <= 5 ? v >> (5 - j) : v << (j - 5);
+        pass |= s & (0x01010101u << j);
     }
     return pass;
 }
 
-// Window-sliced evaluation of the first chunk with a B-bit counter.
-// P[j] holds position j's membership masks broadcast to whole words.
-// Returns the windows still at or below k; cnt receives the counter planes.
-template <int B>
-__device__ __forceinline__ uint32_t survivors_window_sliced(uint2 a, uint2 b,
-                                                            const uint4 *__restrict__ P,
-                                                            uint32_t k, uint32_t dead,
-                                                            uint32_t (&cnt)[B > 0 ? B : 1])
+// Window-sliced first chunk with a thermometer counter of K+1 levels over the
+// listed positions, for all groups of the lane at once.  alive[g] receives
+// the windows still at or below K.
+template <int K>
+__device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                    const uint4 *__restrict__ list,
+                                                    uint32_t n_single, uint32_t n_general,
+                                                    const uint32_t (&valid)[G],
+                                                    uint32_t (&alive)[G])
 {
-    const uint32_t v0 = (1u << B) - (k + 1u);  // B == 0 only for k == 0
+    uint32_t L[G][K + 1];
 #pragma unroll
-    for (int i = 0; i < B; ++i) cnt[i] = ((v0 >> i) & 1u) ? 0xffffffffu : 0u;
+    for (int g = 0; g < G; ++g)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const uint4 Pj = P[j];
-        const uint32_t lo = __funnelshift_r(a.x, b.x, j);
-        const uint32_t hi = __funnelshift_r(a.y, b.y, j);
-        uint32_t carry = ~class_match(lo, hi, Pj);
+        for (int i = 0; i <= K; ++i) L[g][i] = ~valid[g];  // invalid windows sit at every level
+    auto dead_all = [&]() {
+        uint32_t d = kFull;
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const uint32_t t = cnt[i] & carry;
-            cnt[i] ^= carry;
-            carry = t;
+        for (int g = 0; g < G; ++g) d &= L[g][K];
+        return !__any_sync(kFull, ~d);
+    };
+    auto add = [&](int g, uint32_t mis) {
+#pragma unroll
+        for (int i = K; i >= 1; --i) L[g][i] |= L[g][i - 1] & mis;
+        L[g][0] |= mis;
+    };
+    uint32_t e = 0;
+    for (; e + 4 <= n_single; e += 4) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = list[e + u];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t mis[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q[u].x);
+                const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q[u].x);
+                mis[u] = (lo ^ q[u].y) | (hi ^ q[u].z);
+            }
+            if constexpr (K == 0) {
+                L[g][0] |= (mis[0] | mis[1]) | (mis[2] | mis[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(g, mis[u]);
+            }
         }
-        dead |= carry;
-        if ((j & 3) == 3 && dead == 0xffffffffu) break;
-    }
-    return ~dead;
-}
-
-template <int B>
-__device__ __forceinline__ uint32_t counter_value(const uint32_t (&cnt)[B > 0 ? B : 1], uint32_t w,
-                                                  uint32_t k)
-{
-    uint32_t v = 0;
+        if (dead_all()) {
 #pragma unroll
-    for (int i = 0; i < B; ++i) v |= ((cnt[i] >> w) & 1u) << i;
-    return v - ((1u << B) - (k + 1u));
+            for (int g = 0; g < G; ++g) alive[g] = 0u;
+            return;
+        }
+    }
+    for (; e < n_single; ++e) {
+        const uint4 q = list[e];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q.x);
+            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q.x);
+            add(g, (lo ^ q.y) | (hi ^ q.z));
+        }
+    }
+    for (uint32_t c = 0; c < n_general; ++c) {
+        const uint32_t s = list[n_single + 2 * c].x;
+        const uint4 M = list[n_single + 2 * c + 1];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, s);
+            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, s);
+            add(g, ~class_match(lo, hi, M));
+        }
+        if ((c & 3) == 3 && dead_all()) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) alive[g] = 0u;
+            return;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
 }
 
-// VARIANT: -1 pattern-sliced, B >= 0 window-sliced with a B-bit counter.
+// One warp tile and its halo, global -> shared, completing on bar.
+__device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, uint2 *dst,
+                                           uint64_t *bar)
+{
+    dev::mbar_arrive_expect_tx(bar, kStageBytes);
+    dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
+}
+
+// VARIANT: -1 pattern-sliced; K in 0..kWsMaxK window-sliced with threshold K.
 template <int VARIANT>
-__global__ void __launch_bounds__(kScanThreads)
-    k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ masks,
+__global__ void __launch_bounds__(kScanThreads, 4)
+    k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status)
 {
     constexpr bool kWS = VARIANT >= 0;
-    constexpr int B = kWS ? VARIANT : 0;
-    constexpr int kWarps = kScanThreads / 32;
+    constexpr int K = kWS ? VARIANT : 0;
 
-    __shared__ __align__(128) uint2 sbuf[2][kTileBlocks + kHaloBlocks];
-    __shared__ __align__(8) uint64_t sbar[2];
-    __shared__ uint4 spos[kWS ? 32 : 1];
-    __shared__ uint32_t swarp[kWarps];
-    __shared__ unsigned long long sbase;
+    __shared__ __align__(128) uint2 sbuf[kScanWarps][2][kStageBlocks];
+    __shared__ __align__(8) uint64_t sbar[kScanWarps][2];
+    __shared__ uint4 slist[kWS ? 64 : 1];
 
-    const int tid = threadIdx.x;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t k = (uint32_t)d.k;
-    const uint4 *__restrict__ M = masks + d.masks;
+    const uint4 *__restrict__ M = arena + d.masks;
     const uint4 M0 = __ldg(M);
+    // run-time constants for the multiply-adds of the pattern-sliced test
+    const uint32_t one = d.two >> 1, m8 = one << 8, m16 = one << 16, m24 = one << 24;
+    const uint32_t k4 = (k < 32u ? k : 0u) * (m24 | m16 | m8 | one);
 
-    if (tid == 0) {
-        dev::mbar_init(&sbar[0], 1);
-        dev::mbar_init(&sbar[1], 1);
+    if (kWS) {
+        const uint32_t len = d.n_single + 2 * d.n_general;
+        for (uint32_t i = threadIdx.x; i < len; i += kScanThreads) slist[i] = __ldg(arena + d.wslist + i);
+        __syncthreads();  // the only CTA-wide barrier: the list is shared by all warps
+    }
+    if (lane == 0) {
+        dev::mbar_init(&sbar[warp][0], 1);
+        dev::mbar_init(&sbar[warp][1], 1);
         dev::fence_mbar_init();
     }
-    if (kWS && tid < 32) {
-        // position tid's membership bits, broadcast over 32 windows
-        spos[tid] = make_uint4(0u - ((M0.x >> tid) & 1u), 0u - ((M0.y >> tid) & 1u),
-                               0u - ((M0.z >> tid) & 1u), 0u - ((M0.w >> tid) & 1u));
-    }
-    __syncthreads();
+    __syncwarp();
 
-    uint64_t tile = blockIdx.x;
-    if (tid == 0 && tile < d.ntiles) {
-        dev::mbar_arrive_expect_tx(&sbar[0], kTileBytes);
-        dev::bulk_g2s(&sbuf[0][0], planes + tile * kTileBlocks, kTileBytes, &sbar[0]);
+    const uint64_t stride = (uint64_t)gridDim.x * kScanWarps;
+    const uint64_t first = (uint64_t)blockIdx.x * kScanWarps + warp;
+    if (lane == 0) {
+        if (first < d.ntiles) issue_tile(planes, first, &sbuf[warp][0][0], &sbar[warp][0]);
+        if (first + stride < d.ntiles)
+            issue_tile(planes, first + stride, &sbuf[warp][1][0], &sbar[warp][1]);
     }
 
-    for (uint32_t it = 0; tile < d.ntiles; ++it, tile += gridDim.x) {
-        const uint32_t s = it & 1u;
-        const uint64_t next = tile + gridDim.x;
-        if (tid == 0 && next < d.ntiles) {
-            dev::fence_proxy_async_smem();
-            dev::mbar_arrive_expect_tx(&sbar[s ^ 1u], kTileBytes);
-            dev::bulk_g2s(&sbuf[s ^ 1u][0], planes + next * kTileBlocks, kTileBytes, &sbar[s ^ 1u]);
-        }
-        const bool ok = dev::mbar_wait_bounded(&sbar[s], (it >> 1) & 1u, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+    uint32_t it = 0;
+    for (uint64_t tile = first; tile < d.ntiles; tile += stride, ++it) {
+        const int s = it & 1;
+        const bool ok = dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
+        if (__any_sync(kFull, !ok)) {
+            if (lane == 0) {
                 atomicOr(status, kDevTimeout);
-                // let copies still in flight land before the CTA leaves
-                dev::mbar_wait_bounded(&sbar[s], (it >> 1) & 1u, kWaitLimitNs);
-                if (next < d.ntiles)
-                    dev::mbar_wait_bounded(&sbar[s ^ 1u], ((it + 1) >> 1) & 1u, kWaitLimitNs);
+                // let the copies this warp still has in flight land before it leaves
+                dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
+                if (tile + stride < d.ntiles)
+                    dev::mbar_wait_bounded(&sbar[warp][s ^ 1], ((it + 1) >> 1) & 1u, kWaitLimitNs);
             }
             return;
         }
-
-        const uint64_t blk = tile * kTileBlocks + (uint64_t)tid;  // first window = 32*blk
-        const uint64_t w0 = blk * 32ull;
-        const uint32_t valid = w0 >= d.nwin ? 0u
-                               : (d.nwin - w0 >= 32 ? 0xffffffffu
-                                                    : (1u << (uint32_t)(d.nwin - w0)) - 1u);
-        const uint2 a = sbuf[s][tid];
-        const uint2 b = sbuf[s][tid + 1];
-
-        uint32_t pass;
-        if constexpr (kWS) {
-            uint32_t cnt[B > 0 ? B : 1];
-            pass = valid ? survivors_window_sliced<B>(a, b, spos, k, ~valid, cnt) : 0u;
-            if (d.nchunks > 1) {
-                uint32_t sv = pass;
-                while (sv) {
-                    const uint32_t w = __ffs(sv) - 1;
-                    sv &= sv - 1;
-                    const uint32_t c = window_count_from(planes, blk, w, M, 1, d.nchunks,
-                                                         counter_value<B>(cnt, w, k), k);
-                    if (c > k) pass &= ~(1u << w);
-                }
-            }
-        } else {
-            pass = valid ? survivors_pattern_sliced(a, b, M0, k) & valid : 0u;
-            if (d.nchunks > 1) {
-                uint32_t sv = pass;
-                while (sv) {
-                    const uint32_t w = __ffs(sv) - 1;
-                    sv &= sv - 1;
-                    const uint32_t c0 = __popc(~class_match(__funnelshift_r(a.x, b.x, w),
-                                                            __funnelshift_r(a.y, b.y, w), M0));
-                    const uint32_t c = window_count_from(planes, blk, w, M, 1, d.nchunks, c0, k);
-                    if (c > k) pass &= ~(1u << w);
-                }
-            }
-        }
-
-        // ---- hits of this tile, in window order ----
-        if (__syncthreads_or(pass != 0u)) {
-            const uint32_t nh = __popc(pass);
-            uint32_t incl = nh;
+        uint2 a[G], b[G];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((tid & 31) >= o) incl += v;
-            }
-            if ((tid & 31) == 31) swarp[tid >> 5] = incl;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t run = 0;
-                for (int q = 0; q < kWarps; ++q) {
-                    const uint32_t t = swarp[q];
-                    swarp[q] = run;
-                    run += t;
-                }
-                const unsigned long long base = atomicAdd(cursor, (unsigned long long)run);
-                table[d.tile0 + tile] = TileEntry{base, run, 0u};
-                sbase = base;
-            }
-            __syncthreads();
-            unsigned long long q = sbase + swarp[tid >> 5] + (incl - nh);
-            uint32_t hm = pass;
-            while (hm) {
-                const uint32_t w = __ffs(hm) - 1;
-                hm &= hm - 1;
-                if (q < cap) {
-                    const uint32_t c = window_count_from(planes, blk, w, M, 0, d.nchunks, 0u, k);
-                    tmp[q] = pm_hit{(uint32_t)(w0 + w), c};
-                }
-                ++q;
-            }
-        } else if (tid == 0) {
-            table[d.tile0 + tile] = TileEntry{0ull, 0u, 0u};
+        for (int g = 0; g < G; ++g) {
+            a[g] = sbuf[warp][s][32 * g + lane];
+            b[g] = sbuf[warp][s][32 * g + lane + 1];
         }
-        __syncthreads();  // sbuf[s] and swarp are reused
+        __syncwarp();
+        if (lane == 0 && tile + 2 * stride < d.ntiles) {
+            dev::fence_proxy_async_smem();
+            issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
+        }
+
+        uint64_t blk[G];
+        uint32_t valid[G], pass[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;  // windows start at 32*blk
+            const uint64_t w0 = blk[g] * 32ull;
+            valid[g] = w0 >= d.nwin ? 0u
+                       : (d.nwin - w0 >= 32 ? kFull : (1u << (uint32_t)(d.nwin - w0)) - 1u);
+        }
+        if constexpr (kWS) {
+            alive_window_sliced<K>(a, b, slist, d.n_single, d.n_general, valid, pass);
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                uint32_t t = 0u;
+                if (k > 31u) t = valid[g];
+                else if (valid[g]) t = untranspose(pass_pattern_sliced(a[g], b[g], M0, k4, one, m8,
+                                                                       m16, m24)) & valid[g];
+                pass[g] = t;
+            }
+        }
+        // Both evaluations are exact for m <= 32.  Longer patterns: count every
+        // remaining window exactly and drop those past k.
+        if (d.nchunks > 1) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                uint32_t sv = pass[g];
+                while (sv) {
+                    const uint32_t w = __ffs(sv) - 1;
+                    sv &= sv - 1;
+                    if (window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u, k) > k)
+                        pass[g] &= ~(1u << w);
+                }
+            }
+        }
+
+        // ---- hits of this warp tile, in window order (warp-aggregated atomic) ----
+        uint32_t anyp = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) anyp |= pass[g];
+        if (__any_sync(kFull, anyp != 0u)) {
+            uint32_t incl[G], tot[G];
+            uint32_t total = 0;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const uint32_t nh = __popc(pass[g]);
+                incl[g] = nh;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, incl[g], o);
+                    if (lane >= o) incl[g] += v;
+                }
+                tot[g] = __shfl_sync(kFull, incl[g], 31);
+                total += tot[g];
+            }
+            unsigned long long base = 0;
+            if (lane == 0) {
+                base = atomicAdd(cursor, (unsigned long long)total);
+                table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
+            }
+            base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                unsigned long long q = base + incl[g] - __popc(pass[g]);
+                uint32_t hm = pass[g];
+                while (hm) {
+                    const uint32_t w = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    if (q < cap) {
+                        const uint32_t c = window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u, k);
+                        tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
+                    }
+                    ++q;
+                }
+                base += tot[g];
+            }
+        } else if (lane == 0) {
+            table[d.tile0 + tile] = TileEntry{0u, 0u};
+        }
     }
 }
 
@@ -255,14 +360,15 @@ const void *kernel_ptr()
 
 const void *select_kernel(Variant v, int32_t k)
 {
-    if (v == Variant::kWindowSliced) {
-        switch (ws_bits(k)) {
+    if (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) {
+        switch (k) {
         case 0: return kernel_ptr<0>();
         case 1: return kernel_ptr<1>();
         case 2: return kernel_ptr<2>();
         case 3: return kernel_ptr<3>();
         case 4: return kernel_ptr<4>();
         case 5: return kernel_ptr<5>();
+        case 6: return kernel_ptr<6>();
         default: break;
         }
     }
@@ -271,38 +377,37 @@ const void *select_kernel(Variant v, int32_t k)
 
 }  // namespace
 
-int ws_bits(int32_t k)
+Variant auto_variant(const PatDesc &d)
 {
-    if (k < 0) return -1;
-    int b = 0;
-    while ((1ll << b) < (long long)k + 1) ++b;
-    return b <= 5 ? b : -1;
+    // window-sliced wins while few positions decide a window (small k)
+    return d.k <= 4 ? Variant::kWindowSliced : Variant::kPatternSliced;
 }
 
-int scan_grid_limit(Variant v, int device)
+int scan_grid_limit(Variant v, int32_t k, int device)
 {
-    static int cache[2][64] = {};
-    const int vi = (int)v;
+    static int cache[64][kWsMaxK + 2] = {};
     if (device < 0 || device >= 64) return 0;
-    if (cache[vi][device]) return cache[vi][device];
+    const int slot = (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) ? k : kWsMaxK + 1;
+    if (cache[device][slot]) return cache[device][slot];
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(v, 0), kScanThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(v, k), kScanThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    cache[vi][device] = sms * per_sm;
-    return cache[vi][device];
+    cache[device][slot] = sms * per_sm;
+    return cache[device][slot];
 }
 
-cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *masks,
+cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *arena,
                         TileEntry *table, pm_hit *tmp, uint64_t cap, unsigned long long *cursor,
                         uint32_t *status, int grid, cudaStream_t stream)
 {
     if (d.ntiles == 0) return cudaSuccess;
-    if ((uint64_t)grid > d.ntiles) grid = (int)d.ntiles;
-    if (v == Variant::kWindowSliced && ws_bits(d.k) < 0) v = Variant::kPatternSliced;
+    const uint64_t ctas_needed = (d.ntiles + kScanWarps - 1) / kScanWarps;
+    if ((uint64_t)grid > ctas_needed) grid = (int)ctas_needed;
+    if (grid < 1) grid = 1;
     const void *fn = select_kernel(v, d.k);
     PatDesc dd = d;
-    void *args[] = {(void *)&planes, (void *)&dd, (void *)&masks, (void *)&table,
+    void *args[] = {(void *)&planes, (void *)&dd, (void *)&arena, (void *)&table,
                     (void *)&tmp,    (void *)&cap, (void *)&cursor, (void *)&status};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kScanThreads), args, 0, stream);
 }

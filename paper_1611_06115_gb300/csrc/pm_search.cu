@@ -106,27 +106,34 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
         return PM_E_ARG;
     }
 
-    // ---- descriptors and the mask arena ----
+    if (capacity > kMaxCapacity) {
+        set_error("pm_search: capacity %llu exceeds %llu", (unsigned long long)capacity,
+                  (unsigned long long)kMaxCapacity);
+        return PM_E_TOO_LARGE;
+    }
+
+    // ---- descriptors and the arena (chunk masks, window-sliced lists) ----
     std::vector<PatDesc> desc(npat);
-    std::unordered_map<const pm_pattern *, uint64_t> where;
+    struct Placed { uint64_t masks, list; };
+    std::unordered_map<const pm_pattern *, Placed> where;
     uint64_t nmask = 0, entries = 0;
     for (uint32_t p = 0; p < npat; ++p) {
         const pm_pattern *pt = patterns[p];
         auto it = where.find(pt);
-        uint64_t mo;
         if (it == where.end()) {
-            mo = nmask;
-            where.emplace(pt, mo);
-            nmask += pt->nchunks;
-        } else {
-            mo = it->second;
+            Placed pl{nmask, nmask + pt->nchunks};
+            it = where.emplace(pt, pl).first;
+            nmask += pt->nchunks + pt->n_single + 2ull * pt->n_general;
         }
         PatDesc &d = desc[p];
         d.m = pt->m;
         d.nchunks = pt->nchunks;
         d.k = k[p];
-        d.pad0 = 0;
-        d.masks = mo;
+        d.n_single = pt->n_single;
+        d.n_general = pt->n_general;
+        desc_constants(d);
+        d.masks = it->second.masks;
+        d.wslist = it->second.list;
         d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
         d.tile0 = entries;
         d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
@@ -170,8 +177,12 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
     rc = acquire_pinned(dev, up_bytes, &slot);
     if (!rc) {
         char *h = (char *)slot->ptr;
-        for (const auto &kv : where)
-            std::memcpy(h + kv.second * sizeof(uint4), kv.first->masks, kv.first->nchunks * sizeof(uint4));
+        for (const auto &kv : where) {
+            const pm_pattern *pt = kv.first;
+            std::memcpy(h + kv.second.masks * sizeof(uint4), pt->masks, pt->nchunks * sizeof(uint4));
+            std::memcpy(h + kv.second.list * sizeof(uint4), pt->wslist,
+                        (pt->n_single + 2ull * pt->n_general) * sizeof(uint4));
+        }
         uint64_t *ht0 = (uint64_t *)(h + nmask * sizeof(uint4));
         for (uint32_t p = 0; p < npat; ++p) ht0[p] = desc[p].tile0;
         ht0[npat] = entries;
@@ -187,12 +198,11 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
 
     // ---- one scan launch per pattern ----
     for (uint32_t p = 0; !rc && p < npat; ++p) {
-        Variant v;
+        Variant v = auto_variant(desc[p]);
         if (o.variant == PM_VARIANT_PATTERN_SLICED) v = Variant::kPatternSliced;
         else if (o.variant == PM_VARIANT_WINDOW_SLICED) v = Variant::kWindowSliced;
-        else v = ws_bits(desc[p].k) >= 0 && ws_bits(desc[p].k) <= 2 ? Variant::kWindowSliced
-                                                                     : Variant::kPatternSliced;
-        const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, dev);
+        if (v == Variant::kWindowSliced && desc[p].k > kWsMaxK) v = Variant::kPatternSliced;
+        const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, desc[p].k, dev);
         if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p], st);
         rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
                                      d_cursor, d_status, grid, st),
