@@ -186,6 +186,50 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                        const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
                        uint64_t *needed, const pm_options *options, void *stream);
 
+/* ----------------------------------------------------------------- batch */
+
+/*
+ * Batched search: many (pattern, k) pairs of uneven m and k in ONE
+ * persistent kernel launch over the resident text (Eq. 4 with the early
+ * stop of Sec. 2.4-2.5, tiles with m-1 overlap as in Sec. 2.6).  Each text
+ * tile is staged once and every pattern of a group runs over it, so the
+ * text is read from device memory about once for the whole batch.  Results
+ * are identical to pm_search's for the same pairs.
+ *
+ * pm_batch_create  copies the patterns' compiled data and k to the device
+ *                  and allocates all scratch for up to `capacity` hits
+ *                  (cudaMalloc; about 56 bytes per unit of capacity).  The
+ *                  pattern handles may be freed afterwards; the text must
+ *                  outlive the batch.  Waits for its uploads.
+ * options          NULL for defaults, or:
+ *                    group     patterns per work item (default 8);
+ *                    grid      CTAs of the persistent launch (default: as
+ *                              many as the device keeps resident);
+ *                    ws_max_k  largest k evaluated window-sliced (0..6;
+ *                              default 4; -1 for none).
+ * pm_batch_run     runs the batch into device buffers: hits (capacity
+ *                  records) and offsets (npat+1; pattern p's hits are
+ *                  hits[offsets[p] .. offsets[p+1]), sorted by location;
+ *                  offsets[npat] is the total, PM_TOTAL_ERROR after a
+ *                  device-side failure).  If the total exceeds capacity no
+ *                  hit is written.  It allocates nothing and does not wait:
+ *                  all work is queued on `stream`, so the call may be
+ *                  captured in a CUDA graph and replayed.  Runs of one batch
+ *                  must not overlap on the GPU (they share its scratch).
+ */
+typedef struct pm_batch_options {
+    int32_t group;
+    int32_t grid;
+    int32_t ws_max_k;
+} pm_batch_options;
+
+pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                          const int32_t *k, uint64_t capacity, const pm_batch_options *options,
+                          void *stream, pm_batch **out);
+pm_status pm_batch_run(pm_batch *batch, pm_hit *hits, uint64_t *offsets, void *stream);
+uint64_t pm_batch_capacity(const pm_batch *batch);
+void pm_batch_free(pm_batch *batch);
+
 /*
  * pm_search_noalloc -- pm_search for callers that must not allocate memory.
  * The paper has no counterpart: this is a deployment concern, not part of

@@ -13,5 +13,5 @@ from ._native import (PM_E_ARG, PM_E_CUDA, PM_E_NOMEM, PM_E_OVERFLOW, PM_E_SYMBO
                       PM_E_TIMEOUT, PM_E_TOO_LARGE, PM_OK, PM_TOTAL_ERROR,
                       PM_VARIANT_AUTO, PM_VARIANT_PATTERN_SLICED, PM_VARIANT_WINDOW_SLICED,
                       NativeLibraryMissing, PmError, lib)
-from .api import (Pattern, SearchResult, Text, pm_compile_pattern, pm_encode_text,  # noqa: F401
-                  pm_search, pm_search_ex)
+from .api import (Batch, GraphedBatch, Pattern, SearchResult, Text,  # noqa: F401
+                  pm_compile_pattern, pm_encode_text, pm_search, pm_search_ex)

@@ -48,6 +48,10 @@ class pm_options(ctypes.Structure):
                 ("events", ctypes.POINTER(ctypes.c_void_p))]
 
 
+class pm_batch_options(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("grid", ctypes.c_int32), ("ws_max_k", ctypes.c_int32)]
+
+
 # Every function include/pm.h declares, with (restype, argtypes).
 _vp, _u64, _u32, _i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
 SIGNATURES = {
@@ -66,6 +70,11 @@ SIGNATURES = {
                             ctypes.POINTER(_u64), ctypes.POINTER(pm_options), _vp]),
     "pm_search_noalloc": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _vp, _u64,
                                  _vp, ctypes.POINTER(_u64), _vp]),
+    "pm_batch_create": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _u64,
+                               ctypes.c_void_p, _vp, ctypes.POINTER(_vp)]),
+    "pm_batch_run": (_i32, [_vp, _vp, _vp, _vp]),
+    "pm_batch_capacity": (_u64, [_vp]),
+    "pm_batch_free": (None, [_vp]),
     "pm_status_string": (ctypes.c_char_p, [_i32]),
     "pm_last_error": (ctypes.c_char_p, []),
 }

@@ -210,3 +210,82 @@ def pm_search(text: Text, patterns, k, capacity: int | None = None, out: str = "
               stream=None) -> SearchResult:
     """pm_search of include/pm.h (default options)."""
     return pm_search_ex(text, patterns, k, capacity=capacity, out=out, stream=stream)
+
+
+class Batch:
+    """A batch of (pattern, k) pairs resident on the device (pm_batch_create).
+
+    ``run`` queues one persistent launch plus the ordering kernels into the
+    given device buffers without allocating or waiting, so it can be
+    captured in a CUDA graph (see ``GraphedBatch``).
+    """
+
+    def __init__(self, text: Text, patterns, k, capacity: int, group: int = 0, grid: int = 0,
+                 ws_max_k: int = 0, stream=None):
+        pats = list(patterns)
+        self.npat = len(pats)
+        ks = [int(k)] * self.npat if np.isscalar(k) else [int(x) for x in k]
+        if len(ks) != self.npat:
+            raise ValueError("one k per pattern")
+        handles = (ctypes.c_void_p * max(self.npat, 1))(*[p.handle for p in pats])
+        karr = (ctypes.c_int32 * max(self.npat, 1))(*ks)
+        opts = N.pm_batch_options(group, grid, ws_max_k)
+        out = ctypes.c_void_p()
+        N.check(N.lib().pm_batch_create(text.handle, handles, self.npat, karr, int(capacity),
+                                        ctypes.cast(ctypes.byref(opts), ctypes.c_void_p),
+                                        _stream(stream), ctypes.byref(out)), "pm_batch_create")
+        self._h = out
+        self._text = text  # the text must outlive the batch
+        self.capacity = int(capacity)
+
+    def buffers(self, device=None) -> SearchResult:
+        dev = torch.cuda.current_device() if device is None else device
+        return SearchResult(torch.empty((max(self.capacity, 1), 2), dtype=torch.int32, device=dev),
+                            torch.empty(self.npat + 1, dtype=torch.int64, device=dev))
+
+    def run(self, out: SearchResult | None = None, stream=None) -> SearchResult:
+        """Queue the batch into ``out`` (device buffers; allocated if None).
+        Asynchronous: read ``out.total`` after the stream; a total above the
+        capacity means nothing was written."""
+        if out is None:
+            out = self.buffers()
+        N.check(N.lib().pm_batch_run(self._h, ctypes.c_void_p(out.hits.data_ptr()),
+                                     ctypes.c_void_p(out.offsets.data_ptr()), _stream(stream)),
+                "pm_batch_run")
+        return out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            N.lib().pm_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class GraphedBatch:
+    """A Batch run captured once in a CUDA graph and replayed.
+
+    Replays reuse the same output buffers (``self.out``); each replay
+    rewrites them completely.
+    """
+
+    def __init__(self, batch: Batch):
+        self.batch = batch
+        self.out = batch.buffers()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            batch.run(self.out, stream=s)  # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            batch.run(self.out, stream=torch.cuda.current_stream())
+
+    def replay(self) -> SearchResult:
+        self.graph.replay()
+        return self.out

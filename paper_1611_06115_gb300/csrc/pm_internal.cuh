@@ -63,8 +63,9 @@ struct PatDesc {
     int32_t k;           // allowed mismatches (>= 0)
     uint32_t n_single;   // window-sliced list: one-letter entries
     uint32_t n_general;  // window-sliced list: other-class entry pairs
-    uint32_t two;        // 2 and 2^27, given at run time so that the multiply-adds
-    uint32_t c27;        //   built on them stay multiply-adds (FMA pipe)
+    uint32_t two;        // the constant 2, given at run time so that the multiply-adds
+                         //   built on it stay multiply-adds (FMA pipe)
+    uint32_t variant;    // Variant chosen for this pattern (batched kernel)
     uint32_t pad0;
     uint64_t masks;      // chunk 0 in the arena (uint4 units)
     uint64_t wslist;     // window-sliced list in the arena (uint4 units)
@@ -104,9 +105,28 @@ Variant auto_variant(const PatDesc &d);
 inline void desc_constants(PatDesc &d)
 {
     d.two = 2u;
-    d.c27 = 1u << 27;
+    d.variant = 0u;
     d.pad0 = 0u;
 }
+
+// A (pattern, tile) segment of hits left by the batched scan: key =
+// pattern * ntiles + tile, the hits in window order at tmp[src .. src+count).
+struct SegRecord {
+    unsigned long long key;
+    uint32_t src;
+    uint32_t count;
+};
+
+// Radix sort of segment records by key (pm_sort.cu).  The live count is
+// *n_dev (at most n_max); key_bits bounds the keys.  *sorted receives the
+// buffer that holds the result (recs or the scratch copy).
+size_t sort_scratch_bytes(uint64_t n_max);
+cudaError_t launch_sort_records(SegRecord *recs, uint64_t n_max, const unsigned long long *n_dev,
+                                int key_bits, void *scratch, cudaStream_t stream,
+                                SegRecord **sorted);
+cudaError_t launch_records_to_entries(const SegRecord *recs, uint64_t n_max,
+                                      const unsigned long long *n_dev, TileEntry *entries,
+                                      cudaStream_t stream);
 
 // Ordering: exclusive scan of table counts, per-pattern CSR offsets, and the
 // gather of hits into their final places (pm_order.cu).  Needs
@@ -116,6 +136,16 @@ cudaError_t launch_order(const TileEntry *table, uint64_t entries, const uint64_
                          uint32_t npat, const pm_hit *tmp, pm_hit *hits, uint64_t cap,
                          uint64_t *offsets, const uint32_t *status, void *scratch,
                          cudaStream_t stream);
+
+// The same for segment records already sorted by (pattern, tile), whose
+// number lives in device memory (*n_dev, at most n_max): CSR offsets from
+// per-pattern counts, hits gathered unless hits_found exceeds cap.
+cudaError_t launch_order_records(const TileEntry *entries, uint64_t n_max,
+                                 const unsigned long long *n_dev,
+                                 const unsigned long long *pat_counts, uint32_t npat,
+                                 const unsigned long long *hits_found, const pm_hit *tmp,
+                                 pm_hit *hits, uint64_t cap, uint64_t *offsets,
+                                 const uint32_t *status, void *scratch, cudaStream_t stream);
 
 // Text coding kernel (pm_text.cu).
 cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol,

@@ -1,12 +1,17 @@
 // Ordering of hits (output contract: per pattern, sorted by location).
 //
 // The scan kernels leave each (pattern, tile) segment of hits in window
-// order somewhere in a scratch buffer and record {where, how many} in a
-// tile table whose entries run pattern-major, tile-minor, i.e. already in
-// the output order.  An exclusive prefix sum over the table's counts gives
-// each segment its final place; per-pattern CSR offsets are the prefix at
-// each pattern's first entry; a gather copies the segments.  No comparison
-// sort is needed.
+// order somewhere in a scratch buffer and describe it by an entry {count,
+// src}.  Entries are either a dense table running pattern-major, tile-minor
+// (per-pattern launches), or segment records sorted by (pattern, tile)
+// (batched launch); either way they are already in output order.  An
+// exclusive prefix sum over the counts gives each segment its final place,
+// per-pattern CSR offsets come from the same sums, and a gather copies the
+// segments.  No comparison sort of hits is needed.
+//
+// The number of entries may live in device memory (n_dev, capped by the
+// host-side bound n_max that sizes the grids), so that a batched run needs
+// no host round trip.
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -16,8 +21,15 @@ constexpr int kOrdThreads = 256;
 constexpr int kOrdItems = 16;
 constexpr uint64_t kSeg = (uint64_t)kOrdThreads * kOrdItems;  // entries per block
 
+__device__ __forceinline__ uint64_t entry_count(uint64_t n_max, const unsigned long long *n_dev)
+{
+    if (!n_dev) return n_max;
+    const uint64_t n = *n_dev;
+    return n < n_max ? n : n_max;
+}
+
 // Exclusive prefix sum over a CTA; returns this thread's prefix and sets
-// *total to the CTA sum.
+// *total (a __shared__ variable) to the CTA sum.
 __device__ __forceinline__ unsigned long long block_exclusive(unsigned long long v,
                                                               unsigned long long *total)
 {
@@ -38,7 +50,7 @@ __device__ __forceinline__ unsigned long long block_exclusive(unsigned long long
             sw[q] = run;
             run += t;
         }
-        *total = run;  // the caller passes a __shared__ variable
+        *total = run;
     }
     __syncthreads();
     const unsigned long long r = sw[warp] + incl - v;
@@ -47,10 +59,11 @@ __device__ __forceinline__ unsigned long long block_exclusive(unsigned long long
 }
 
 __global__ void __launch_bounds__(kOrdThreads)
-    k_reduce(const TileEntry *__restrict__ table, uint64_t entries,
-             unsigned long long *__restrict__ partial)
+    k_reduce(const TileEntry *__restrict__ table, uint64_t n_max,
+             const unsigned long long *__restrict__ n_dev, unsigned long long *__restrict__ partial)
 {
     __shared__ unsigned long long stotal;
+    const uint64_t entries = entry_count(n_max, n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * kSeg + (uint64_t)threadIdx.x * kOrdItems;
     unsigned long long s = 0;
 #pragma unroll
@@ -78,10 +91,12 @@ __global__ void __launch_bounds__(kOrdThreads)
 }
 
 __global__ void __launch_bounds__(kOrdThreads)
-    k_dest(const TileEntry *__restrict__ table, uint64_t entries,
+    k_dest(const TileEntry *__restrict__ table, uint64_t n_max,
+           const unsigned long long *__restrict__ n_dev,
            const unsigned long long *__restrict__ partial, unsigned long long *__restrict__ dest)
 {
     __shared__ unsigned long long stotal;
+    const uint64_t entries = entry_count(n_max, n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * kSeg + (uint64_t)threadIdx.x * kOrdItems;
     uint32_t c[kOrdItems];
     unsigned long long s = 0;
@@ -113,14 +128,36 @@ __global__ void k_offsets(const uint64_t *__restrict__ pat_tile0, uint32_t npat,
     offsets[p] = e < entries ? (uint64_t)dest[e] : (uint64_t)*total;
 }
 
-// One warp per table entry: copy its segment to its final place.
+// One CTA: CSR offsets from per-pattern hit counts (exclusive prefix sum),
+// the total at [npat] (PM_TOTAL_ERROR after a device-side failure).
 __global__ void __launch_bounds__(kOrdThreads)
-    k_gather(const TileEntry *__restrict__ table, uint64_t entries,
+    k_offsets_from_counts(const unsigned long long *__restrict__ counts, uint32_t npat,
+                          const uint32_t *__restrict__ status, uint64_t *__restrict__ offsets)
+{
+    __shared__ unsigned long long stotal;
+    unsigned long long carry = 0;
+    for (uint64_t off = 0; off < npat; off += kOrdThreads) {
+        const uint64_t i = off + threadIdx.x;
+        const unsigned long long v = i < npat ? counts[i] : 0ull;
+        const unsigned long long e = block_exclusive(v, &stotal);
+        if (i < npat) offsets[i] = carry + e;
+        carry += stotal;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offsets[npat] = (*status & kDevTimeout) ? PM_TOTAL_ERROR : carry;
+}
+
+// One warp per entry: copy its segment to its final place.
+__global__ void __launch_bounds__(kOrdThreads)
+    k_gather(const TileEntry *__restrict__ table, uint64_t n_max,
+             const unsigned long long *__restrict__ n_dev,
              const unsigned long long *__restrict__ dest, const unsigned long long *__restrict__ total,
              const uint32_t *__restrict__ status, const pm_hit *__restrict__ tmp,
              pm_hit *__restrict__ hits, uint64_t cap)
 {
+    // total: all hits found (nothing is written when they do not fit)
     if (*total > cap || (*status & kDevTimeout)) return;
+    const uint64_t entries = entry_count(n_max, n_dev);
     const uint64_t warps = (uint64_t)gridDim.x * (kOrdThreads / 32);
     const int lane = threadIdx.x & 31;
     for (uint64_t e = (uint64_t)blockIdx.x * (kOrdThreads / 32) + (threadIdx.x >> 5); e < entries;
@@ -128,8 +165,35 @@ __global__ void __launch_bounds__(kOrdThreads)
         const TileEntry te = table[e];
         if (te.count == 0) continue;
         const unsigned long long d = dest[e];
-        for (uint32_t i = lane; i < te.count; i += 32) hits[d + i] = tmp[te.src + i];
+        for (uint32_t i = lane; i < te.count; i += 32) hits[d + i] = tmp[(uint64_t)te.src + i];
     }
+}
+
+// prefix sums of the entry counts: dest[e] and the total (partial[nblk])
+void launch_dest(const TileEntry *table, uint64_t n_max, const unsigned long long *n_dev,
+                 unsigned long long *partial, unsigned long long *dest, cudaStream_t stream)
+{
+    const uint64_t nblk = (n_max + kSeg - 1) / kSeg;
+    if (nblk > 0) k_reduce<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, n_max, n_dev, partial);
+    k_scan_partials<<<1, kOrdThreads, 0, stream>>>(partial, nblk);
+    if (nblk > 0)
+        k_dest<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, n_max, n_dev, partial, dest);
+}
+
+void launch_gather(const TileEntry *table, uint64_t n_max, const unsigned long long *n_dev,
+                   const unsigned long long *dest, const unsigned long long *total,
+                   const uint32_t *status, const pm_hit *tmp, pm_hit *hits, uint64_t cap,
+                   cudaStream_t stream)
+{
+    if (n_max == 0) return;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (n_max + (kOrdThreads / 32) - 1) / (kOrdThreads / 32);
+    uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
+    if (grid < 1) grid = 1;
+    k_gather<<<(unsigned)grid, kOrdThreads, 0, stream>>>(table, n_max, n_dev, dest, total, status,
+                                                         tmp, hits, cap);
 }
 
 }  // namespace
@@ -150,25 +214,26 @@ cudaError_t launch_order(const TileEntry *table, uint64_t entries, const uint64_
     auto *partial = (unsigned long long *)scratch;
     auto *dest = partial + nblk + 1;
     const unsigned long long *total = partial + nblk;
-    if (nblk > 0) {
-        k_reduce<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, entries, partial);
-    }
-    k_scan_partials<<<1, kOrdThreads, 0, stream>>>(partial, nblk);
-    if (nblk > 0) {
-        k_dest<<<(unsigned)nblk, kOrdThreads, 0, stream>>>(table, entries, partial, dest);
-    }
+    launch_dest(table, entries, nullptr, partial, dest, stream);
     k_offsets<<<(npat + 1 + 255) / 256, 256, 0, stream>>>(pat_tile0, npat, entries, dest, total,
                                                           status, offsets);
-    if (entries > 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        uint64_t want = (entries + (kOrdThreads / 32) - 1) / (kOrdThreads / 32);
-        uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
-        if (grid < 1) grid = 1;
-        k_gather<<<(unsigned)grid, kOrdThreads, 0, stream>>>(table, entries, dest, total, status,
-                                                             tmp, hits, cap);
-    }
+    launch_gather(table, entries, nullptr, dest, total, status, tmp, hits, cap, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_records(const TileEntry *entries, uint64_t n_max,
+                                 const unsigned long long *n_dev,
+                                 const unsigned long long *pat_counts, uint32_t npat,
+                                 const unsigned long long *hits_found, const pm_hit *tmp,
+                                 pm_hit *hits, uint64_t cap, uint64_t *offsets,
+                                 const uint32_t *status, void *scratch, cudaStream_t stream)
+{
+    const uint64_t nblk = (n_max + kSeg - 1) / kSeg;
+    auto *partial = (unsigned long long *)scratch;
+    auto *dest = partial + nblk + 1;
+    launch_dest(entries, n_max, n_dev, partial, dest, stream);
+    k_offsets_from_counts<<<1, kOrdThreads, 0, stream>>>(pat_counts, npat, status, offsets);
+    launch_gather(entries, n_max, n_dev, dest, hits_found, status, tmp, hits, cap, stream);
     return cudaGetLastError();
 }
 

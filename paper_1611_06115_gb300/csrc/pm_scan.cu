@@ -33,175 +33,15 @@
 // Windows still at or below k after those 32 positions are counted again one
 // at a time, 32 positions per step, from position 0 until their sum exceeds k
 // or the pattern ends; that count is exact and is what a hit reports.
-#include "pm_internal.cuh"
+#include "pm_scan_impl.cuh"
 
 namespace pm {
 namespace {
 
-using dev::class_match;
+using namespace scan;
 
-constexpr uint32_t kFull = 0xffffffffu;
-constexpr int G = kGroups;
-
-// Mismatch count of window 32*blk + w over chunks c0.., starting from
-// `count`, stopping once it exceeds `limit` (then some value > limit).
-__device__ __forceinline__ uint32_t window_count_from(const uint2 *__restrict__ planes,
-                                                      uint64_t blk, uint32_t w,
-                                                      const uint4 *__restrict__ M,
-                                                      uint32_t c0, uint32_t nchunks,
-                                                      uint32_t count, uint32_t limit)
-{
-    uint2 a = __ldg(planes + blk + c0);
-    for (uint32_t c = c0; c < nchunks; ++c) {
-        const uint2 b = __ldg(planes + blk + c + 1);
-        const uint32_t lo = __funnelshift_r(a.x, b.x, w);
-        const uint32_t hi = __funnelshift_r(a.y, b.y, w);
-        count += __popc(~class_match(lo, hi, __ldg(M + c)));
-        if (count > limit) break;
-        a = b;
-    }
-    return count;
-}
-
-__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
-{
-    uint32_t r;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-    return r;
-}
-
-// The pass masks below use a transposed bit order: window 4j + b of the lane
-// sits at bit 8b + j.  This restores the natural order (window w at bit w).
-__device__ __forceinline__ uint32_t untranspose(uint32_t t)
-{
-    uint32_t r = 0;
-    while (t) {
-        const uint32_t p = __ffs(t) - 1;
-        t &= t - 1;
-        r |= 1u << (4 * (p & 7) + (p >> 3));
-    }
-    return r;
-}
-
-// Pattern-sliced first chunk for one lane's 32 windows; transposed pass mask
-// of the windows with at most k mismatches in positions 0..31 (k <= 31).
-// k4 = k in every byte; one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
-__device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint4 M0, uint32_t k4,
-                                                        uint32_t one, uint32_t m8, uint32_t m16,
-                                                        uint32_t m24)
-{
-    uint32_t pass = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint32_t g[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int w = 4 * j + q;
-            const uint32_t lo = __funnelshift_r(a.x, b.x, w);
-            const uint32_t hi = __funnelshift_r(a.y, b.y, w);
-            g[q] = __popc(class_match(lo, hi, M0));
-        }
-        uint32_t v = mad_lo(g[3], m24, k4);
-        v = mad_lo(g[2], m16, v);
-        v = mad_lo(g[1], m8, v);
-        v = mad_lo(g[0], one, v);
-        // bit 5 of byte q: g[q] + k >= 32; move bits 5, 13, 21, 29 to 8q + j
-        const uint32_t s = j <= 5 ? v >> (5 - j) : v << (j - 5);
-        pass |= s & (0x01010101u << j);
-    }
-    return pass;
-}
-
-// Window-sliced first chunk with a thermometer counter of K+1 levels over the
-// listed positions, for all groups of the lane at once.  alive[g] receives
-// the windows still at or below K.
-template <int K>
-__device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
-                                                    const uint4 *__restrict__ list,
-                                                    uint32_t n_single, uint32_t n_general,
-                                                    const uint32_t (&valid)[G],
-                                                    uint32_t (&alive)[G])
-{
-    uint32_t L[G][K + 1];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-        for (int i = 0; i <= K; ++i) L[g][i] = ~valid[g];  // invalid windows sit at every level
-    auto dead_all = [&]() {
-        uint32_t d = kFull;
-#pragma unroll
-        for (int g = 0; g < G; ++g) d &= L[g][K];
-        return !__any_sync(kFull, ~d);
-    };
-    auto add = [&](int g, uint32_t mis) {
-#pragma unroll
-        for (int i = K; i >= 1; --i) L[g][i] |= L[g][i - 1] & mis;
-        L[g][0] |= mis;
-    };
-    uint32_t e = 0;
-    for (; e + 4 <= n_single; e += 4) {
-        uint4 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = list[e + u];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            uint32_t mis[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q[u].x);
-                const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q[u].x);
-                mis[u] = (lo ^ q[u].y) | (hi ^ q[u].z);
-            }
-            if constexpr (K == 0) {
-                L[g][0] |= (mis[0] | mis[1]) | (mis[2] | mis[3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) add(g, mis[u]);
-            }
-        }
-        if (dead_all()) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) alive[g] = 0u;
-            return;
-        }
-    }
-    for (; e < n_single; ++e) {
-        const uint4 q = list[e];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q.x);
-            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q.x);
-            add(g, (lo ^ q.y) | (hi ^ q.z));
-        }
-    }
-    for (uint32_t c = 0; c < n_general; ++c) {
-        const uint32_t s = list[n_single + 2 * c].x;
-        const uint4 M = list[n_single + 2 * c + 1];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, s);
-            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, s);
-            add(g, ~class_match(lo, hi, M));
-        }
-        if ((c & 3) == 3 && dead_all()) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) alive[g] = 0u;
-            return;
-        }
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
-}
-
-// One warp tile and its halo, global -> shared, completing on bar.
-__device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, uint2 *dst,
-                                           uint64_t *bar)
-{
-    dev::mbar_arrive_expect_tx(bar, kStageBytes);
-    dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
-}
-
-// VARIANT: -1 pattern-sliced; K in 0..kWsMaxK window-sliced with threshold K.
+// VARIANT: -1 pattern-sliced (k <= 31), -2 pattern-sliced over all chunks
+// (k > 31); K in 0..kWsMaxK window-sliced with threshold K.
 template <int VARIANT>
 __global__ void __launch_bounds__(kScanThreads, 4)
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
@@ -209,7 +49,6 @@ __global__ void __launch_bounds__(kScanThreads, 4)
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status)
 {
     constexpr bool kWS = VARIANT >= 0;
-    constexpr int K = kWS ? VARIANT : 0;
 
     __shared__ __align__(128) uint2 sbuf[kScanWarps][2][kStageBlocks];
     __shared__ __align__(8) uint64_t sbar[kScanWarps][2];
@@ -217,12 +56,9 @@ __global__ void __launch_bounds__(kScanThreads, 4)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t k = (uint32_t)d.k;
     const uint4 *__restrict__ M = arena + d.masks;
     const uint4 M0 = __ldg(M);
-    // run-time constants for the multiply-adds of the pattern-sliced test
-    const uint32_t one = d.two >> 1, m8 = one << 8, m16 = one << 16, m24 = one << 24;
-    const uint32_t k4 = (k < 32u ? k : 0u) * (m24 | m16 | m8 | one);
+    const PsConst pc = ps_const(d.two, (uint32_t)d.k);
 
     if (kWS) {
         const uint32_t len = d.n_single + 2 * d.n_general;
@@ -275,77 +111,19 @@ __global__ void __launch_bounds__(kScanThreads, 4)
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;  // windows start at 32*blk
-            const uint64_t w0 = blk[g] * 32ull;
-            valid[g] = w0 >= d.nwin ? 0u
-                       : (d.nwin - w0 >= 32 ? kFull : (1u << (uint32_t)(d.nwin - w0)) - 1u);
+            valid[g] = valid_mask(blk[g], d.nwin);
         }
-        if constexpr (kWS) {
-            alive_window_sliced<K>(a, b, slist, d.n_single, d.n_general, valid, pass);
-        } else {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                uint32_t t = 0u;
-                if (k > 31u) t = valid[g];
-                else if (valid[g]) t = untranspose(pass_pattern_sliced(a[g], b[g], M0, k4, one, m8,
-                                                                       m16, m24)) & valid[g];
-                pass[g] = t;
-            }
-        }
-        // Both evaluations are exact for m <= 32.  Longer patterns: count every
-        // remaining window exactly and drop those past k.
-        if (d.nchunks > 1) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                uint32_t sv = pass[g];
-                while (sv) {
-                    const uint32_t w = __ffs(sv) - 1;
-                    sv &= sv - 1;
-                    if (window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u, k) > k)
-                        pass[g] &= ~(1u << w);
-                }
-            }
-        }
+        tile_pass<VARIANT>(a, b, blk, valid, d, M, M0, slist, pc, planes, pass);
 
         // ---- hits of this warp tile, in window order (warp-aggregated atomic) ----
         uint32_t anyp = 0;
 #pragma unroll
         for (int g = 0; g < G; ++g) anyp |= pass[g];
         if (__any_sync(kFull, anyp != 0u)) {
-            uint32_t incl[G], tot[G];
-            uint32_t total = 0;
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const uint32_t nh = __popc(pass[g]);
-                incl[g] = nh;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t v = __shfl_up_sync(kFull, incl[g], o);
-                    if (lane >= o) incl[g] += v;
-                }
-                tot[g] = __shfl_sync(kFull, incl[g], 31);
-                total += tot[g];
-            }
-            unsigned long long base = 0;
-            if (lane == 0) {
-                base = atomicAdd(cursor, (unsigned long long)total);
-                table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
-            }
-            base = __shfl_sync(kFull, base, 0);
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                unsigned long long q = base + incl[g] - __popc(pass[g]);
-                uint32_t hm = pass[g];
-                while (hm) {
-                    const uint32_t w = __ffs(hm) - 1;
-                    hm &= hm - 1;
-                    if (q < cap) {
-                        const uint32_t c = window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u, k);
-                        tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
-                    }
-                    ++q;
-                }
-                base += tot[g];
-            }
+            uint32_t total;
+            unsigned long long base;
+            emit_tile_hits(pass, blk, d, M, planes, tmp, cap, cursor, total, base);
+            if (lane == 0) table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
         } else if (lane == 0) {
             table[d.tile0 + tile] = TileEntry{0u, 0u};
         }
@@ -372,7 +150,7 @@ const void *select_kernel(Variant v, int32_t k)
         default: break;
         }
     }
-    return kernel_ptr<-1>();
+    return k > 31 ? kernel_ptr<-2>() : kernel_ptr<-1>();
 }
 
 }  // namespace
@@ -385,9 +163,10 @@ Variant auto_variant(const PatDesc &d)
 
 int scan_grid_limit(Variant v, int32_t k, int device)
 {
-    static int cache[64][kWsMaxK + 2] = {};
+    static int cache[64][kWsMaxK + 3] = {};
     if (device < 0 || device >= 64) return 0;
-    const int slot = (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) ? k : kWsMaxK + 1;
+    const int slot = (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) ? k
+                     : (k > 31 ? kWsMaxK + 2 : kWsMaxK + 1);
     if (cache[device][slot]) return cache[device][slot];
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);

@@ -1,0 +1,341 @@
+// Device building blocks shared by the per-pattern and the batched scan
+// kernels (see pm_scan.cu for the method they implement).
+#pragma once
+
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace scan {
+
+using dev::class_match;
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int G = kGroups;
+
+// Mismatch count of window 32*blk + w over chunks c0.., starting from
+// `count`, stopping once it exceeds `limit` (then some value > limit).
+__device__ __forceinline__ uint32_t window_count_from(const uint2 *__restrict__ planes,
+                                                      uint64_t blk, uint32_t w,
+                                                      const uint4 *__restrict__ M,
+                                                      uint32_t c0, uint32_t nchunks,
+                                                      uint32_t count, uint32_t limit)
+{
+    uint2 a = __ldg(planes + blk + c0);
+    for (uint32_t c = c0; c < nchunks; ++c) {
+        const uint2 b = __ldg(planes + blk + c + 1);
+        const uint32_t lo = __funnelshift_r(a.x, b.x, w);
+        const uint32_t hi = __funnelshift_r(a.y, b.y, w);
+        count += __popc(~class_match(lo, hi, __ldg(M + c)));
+        if (count > limit) break;
+        a = b;
+    }
+    return count;
+}
+
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// The pass masks below use a transposed bit order: window 4j + b of the lane
+// sits at bit 8b + j.  This restores the natural order (window w at bit w).
+__device__ __forceinline__ uint32_t untranspose(uint32_t t)
+{
+    uint32_t r = 0;
+    while (t) {
+        const uint32_t p = __ffs(t) - 1;
+        t &= t - 1;
+        r |= 1u << (4 * (p & 7) + (p >> 3));
+    }
+    return r;
+}
+
+// Pattern-sliced first chunk for one lane's 32 windows; transposed pass mask
+// of the windows with at most k mismatches in positions 0..31 (k <= 31).
+// k4 = k in every byte; one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
+__device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint4 M0, uint32_t k4,
+                                                        uint32_t one, uint32_t m8, uint32_t m16,
+                                                        uint32_t m24)
+{
+    uint32_t pass = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = 4 * j + q;
+            const uint32_t lo = __funnelshift_r(a.x, b.x, w);
+            const uint32_t hi = __funnelshift_r(a.y, b.y, w);
+            g[q] = __popc(class_match(lo, hi, M0));
+        }
+        uint32_t v = mad_lo(g[3], m24, k4);
+        v = mad_lo(g[2], m16, v);
+        v = mad_lo(g[1], m8, v);
+        v = mad_lo(g[0], one, v);
+        // bit 5 of byte q: g[q] + k >= 32; move bits 5, 13, 21, 29 to 8q + j
+        const uint32_t s = j <= 5 ? v >> (5 - j) : v << (j - 5);
+        pass |= s & (0x01010101u << j);
+    }
+    return pass;
+}
+
+// A position-list entry from shared memory, or from global memory through
+// the read-only path (every lane reads the same address: one broadcast).
+template <bool kGlobal>
+__device__ __forceinline__ uint4 ld_list(const uint4 *p)
+{
+    if constexpr (kGlobal) return __ldg(p);
+    else return *p;
+}
+
+// Window-sliced first chunk with a thermometer counter of K+1 levels over the
+// listed positions, for all groups of the lane at once.  alive[g] receives
+// the windows still at or below K.
+template <int K, bool kGlobal = false>
+__device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                    const uint4 *__restrict__ list,
+                                                    uint32_t n_single, uint32_t n_general,
+                                                    const uint32_t (&valid)[G],
+                                                    uint32_t (&alive)[G])
+{
+    uint32_t L[G][K + 1];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int i = 0; i <= K; ++i) L[g][i] = ~valid[g];  // invalid windows sit at every level
+    auto dead_all = [&]() {
+        uint32_t d = kFull;
+#pragma unroll
+        for (int g = 0; g < G; ++g) d &= L[g][K];
+        return !__any_sync(kFull, ~d);
+    };
+    auto add = [&](int g, uint32_t mis) {
+#pragma unroll
+        for (int i = K; i >= 1; --i) L[g][i] |= L[g][i - 1] & mis;
+        L[g][0] |= mis;
+    };
+    uint32_t e = 0;
+    for (; e + 4 <= n_single; e += 4) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = ld_list<kGlobal>(list + e + u);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t mis[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q[u].x);
+                const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q[u].x);
+                mis[u] = (lo ^ q[u].y) | (hi ^ q[u].z);
+            }
+            if constexpr (K == 0) {
+                L[g][0] |= (mis[0] | mis[1]) | (mis[2] | mis[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(g, mis[u]);
+            }
+        }
+        if (dead_all()) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) alive[g] = 0u;
+            return;
+        }
+    }
+    for (; e < n_single; ++e) {
+        const uint4 q = ld_list<kGlobal>(list + e);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q.x);
+            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q.x);
+            add(g, (lo ^ q.y) | (hi ^ q.z));
+        }
+    }
+    for (uint32_t c = 0; c < n_general; ++c) {
+        const uint32_t s = ld_list<kGlobal>(list + n_single + 2 * c).x;
+        const uint4 M = ld_list<kGlobal>(list + n_single + 2 * c + 1);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, s);
+            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, s);
+            add(g, ~class_match(lo, hi, M));
+        }
+        if ((c & 3) == 3 && dead_all()) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) alive[g] = 0u;
+            return;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
+}
+
+// One warp tile and its halo, global -> shared, completing on bar.
+__device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, uint2 *dst,
+                                           uint64_t *bar)
+{
+    dev::mbar_arrive_expect_tx(bar, kStageBytes);
+    dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
+}
+
+
+// Window-valid mask of the 32 windows that start in block blk.
+__device__ __forceinline__ uint32_t valid_mask(uint64_t blk, uint64_t nwin)
+{
+    const uint64_t w0 = blk * 32ull;
+    return w0 >= nwin ? 0u : (nwin - w0 >= 32 ? kFull : (1u << (uint32_t)(nwin - w0)) - 1u);
+}
+
+// Pattern-sliced evaluation over all chunks for large k (k > 31, where one
+// chunk cannot decide a window): 32 per-window counts in registers, one
+// chunk after another (chunk c needs blocks blk+c and blk+c+1; blocks 0 and
+// 1 are given), until every window of the warp has passed k (the early stop
+// of Sec. 2.4) or the pattern ends.  Returns the windows whose full count
+// is at most k.
+__device__ __forceinline__ uint32_t pass_multi_chunk(const uint2 *__restrict__ planes, uint64_t blk,
+                                                     const uint4 *__restrict__ M, uint32_t nchunks,
+                                                     uint32_t k, uint32_t valid, uint2 t0, uint2 t1)
+{
+    uint32_t cnt[32];
+#pragma unroll
+    for (int w = 0; w < 32; ++w) cnt[w] = 0;
+    uint32_t alive = valid;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        if (c > 0) {
+            t0 = t1;
+            t1 = __ldg(planes + blk + c + 1);
+        }
+        const uint4 Mc = __ldg(M + c);
+        uint32_t a2 = 0;
+#pragma unroll
+        for (int w = 0; w < 32; ++w) {
+            cnt[w] += __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), Mc));
+            a2 |= (cnt[w] <= k ? 1u : 0u) << w;
+        }
+        alive &= a2;
+        if (!__any_sync(kFull, alive != 0u)) break;
+    }
+    return alive;
+}
+
+// Exact counts of the windows still in `pass` for a pattern longer than 32:
+// each lane counts its own remaining windows, chunk by chunk, and drops
+// those past k.
+__device__ __forceinline__ uint32_t settle_lane(uint32_t pass, uint64_t blk,
+                                                const uint4 *__restrict__ M, uint32_t nchunks,
+                                                uint32_t k, const uint2 *__restrict__ planes)
+{
+    uint32_t sv = pass;
+    while (sv) {
+        const uint32_t w = __ffs(sv) - 1;
+        sv &= sv - 1;
+        if (window_count_from(planes, blk, w, M, 0, nchunks, 0u, k) > k) pass &= ~(1u << w);
+    }
+    return pass;
+}
+
+// Run-time constants of the pattern-sliced byte test for one k.
+struct PsConst {
+    uint32_t one, m8, m16, m24, k4;
+};
+
+__device__ __forceinline__ PsConst ps_const(uint32_t two, uint32_t k)
+{
+    PsConst c;
+    c.one = two >> 1;
+    c.m8 = c.one << 8;
+    c.m16 = c.one << 16;
+    c.m24 = c.one << 24;
+    c.k4 = (k < 32u ? k : 0u) * (c.m24 | c.m16 | c.m8 | c.one);
+    return c;
+}
+
+// The windows of one warp tile that hold the pattern with at most k
+// mismatches: pass[g] bit w for window 32*blk[g] + w.  VARIANT as in k_scan;
+// list (window-sliced only) is the pattern's position list in shared memory.
+template <int VARIANT>
+__device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[G],
+                                          const uint64_t (&blk)[G], const uint32_t (&valid)[G],
+                                          const PatDesc &d, const uint4 *__restrict__ M,
+                                          uint4 M0, const uint4 *__restrict__ list,
+                                          const PsConst &pc, const uint2 *__restrict__ planes,
+                                          uint32_t (&pass)[G])
+{
+    const uint32_t k = (uint32_t)d.k;
+    if constexpr (VARIANT >= 0) {
+        alive_window_sliced<VARIANT>(a, b, list, d.n_single, d.n_general, valid, pass);
+    } else if constexpr (VARIANT == -2) {
+        // k > 31: one chunk cannot decide; count all chunks (exact, nothing to settle)
+#pragma unroll 1
+        for (int g = 0; g < G; ++g)
+            pass[g] = pass_multi_chunk(planes, blk[g], M, d.nchunks, k, valid[g], a[g], b[g]);
+        return;
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t t = 0u;
+            if (valid[g])
+                t = untranspose(pass_pattern_sliced(a[g], b[g], M0, pc.k4, pc.one, pc.m8, pc.m16,
+                                                    pc.m24)) & valid[g];
+            pass[g] = t;
+        }
+    }
+    // Both evaluations are exact for m <= 32.  Longer patterns: count every
+    // remaining window exactly and drop those past k.
+    if (d.nchunks > 1) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
+    }
+}
+
+// Emit the hits of one warp tile in window order through one
+// warp-aggregated atomic on cursor.  Call with the whole warp and only when
+// some lane has a pass bit.  Returns (on every lane) the number of hits and
+// where they start in tmp.
+__device__ __forceinline__ void emit_tile_hits(const uint32_t (&pass)[G], const uint64_t (&blk)[G],
+                                               const PatDesc &d, const uint4 *__restrict__ M,
+                                               const uint2 *__restrict__ planes,
+                                               pm_hit *__restrict__ tmp, uint64_t cap,
+                                               unsigned long long *__restrict__ cursor,
+                                               uint32_t &total_out, unsigned long long &base_out)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t incl[G], tot[G];
+    uint32_t total = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        incl[g] = __popc(pass[g]);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl[g], o);
+            if (lane >= o) incl[g] += v;
+        }
+        tot[g] = __shfl_sync(kFull, incl[g], 31);
+        total += tot[g];
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 0);
+    total_out = total;
+    base_out = base;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        unsigned long long q = base + incl[g] - __popc(pass[g]);
+        uint32_t hm = pass[g];
+        while (hm) {
+            const uint32_t w = __ffs(hm) - 1;
+            hm &= hm - 1;
+            if (q < cap) {
+                const uint32_t c = window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u,
+                                                     (uint32_t)d.k);
+                tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
+            }
+            ++q;
+        }
+        base += tot[g];
+    }
+}
+
+}  // namespace scan
+}  // namespace pm

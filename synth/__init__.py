@@ -191,16 +191,22 @@ def instance(pattern: str, subs: int, rng: np.random.Generator) -> str:
 
 
 class Occupancy:
-    """Non-overlapping intervals already used by planted copies."""
+    """Non-overlapping intervals [a, b) already used by planted copies, kept
+    sorted by start."""
 
     def __init__(self):
         self.iv: list[tuple[int, int]] = []
 
     def free(self, a: int, b: int) -> bool:
-        return all(b <= x or a >= y for x, y in self.iv)
+        import bisect
+        i = bisect.bisect_left(self.iv, (a, b))
+        if i > 0 and self.iv[i - 1][1] > a:
+            return False
+        return i == len(self.iv) or self.iv[i][0] >= b
 
     def take(self, a: int, b: int):
-        self.iv.append((a, b))
+        import bisect
+        bisect.insort(self.iv, (a, b))
 
 
 def plant(text: np.ndarray, pattern: str, count: int, s_max: int,
