@@ -58,6 +58,10 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--workload", choices=("genome", "batched", "serving"), default="genome",
+                    help="genome (the default line); batched and serving print their own lines")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: queries per second")
     return ap.parse_args()
 
 
@@ -431,9 +435,97 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(a):
+    """BATCHED: n = 1e9 Markov text, 4096 patterns (m log-uniform 12..512, k in
+    0..m/8, one planted copy each): one persistent launch (pm_batch, replayed
+    from a CUDA graph) against one launch per pattern (pm_search)."""
+    import torch
+    import paper_1611_06115_gb300 as pm
+    from synth import workloads
+    n = min(a.n, workloads.BATCHED_N)
+    host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    w = workloads.batched(n=n, count=4096, out=host.numpy())
+    text = pm.pm_encode_text(host)
+    cps = [pm.pm_compile_pattern(p) for p in w.patterns]
+    ks = [kk[0] for kk in w.ks]
+    ref = pm.pm_search(text, cps, ks)
+    cap = ref.total + 1024
+    for i, pl in enumerate(w.planted):
+        l, c = ref.pattern(i)
+        found = dict(zip(l.tolist(), c.tolist()))
+        assert all(found.get(loc) == s for loc, s in pl), f"planted copy missed, pattern {i}"
+    g = pm.GraphedBatch(pm.Batch(text, cps, ks, capacity=cap))
+
+    def timed(fn, reps):
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(max(a.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    reps = max(1, min(a.steps, 3))
+    t_batch = timed(g.replay, reps)
+    out = g.out
+    assert out.total == ref.total and np.array_equal(out.numpy()[0], ref.numpy()[0])
+    t_per = timed(lambda: pm.pm_search_ex(text, cps, ks, capacity=cap, sync=False), reps)
+    n_cells = sum((n - len(p) + 1) * len(p) for p in w.patterns)
+    print(json.dumps({
+        "workload": "BATCHED", "metric": METRIC, "n": n, "patterns": len(cps),
+        "value": n_cells / t_batch, "unit": "window-cells/s", "seconds_per_batch": t_batch,
+        "per_pattern_launches": {"value": n_cells / t_per, "seconds": t_per},
+        "batched_over_per_pattern": t_per / t_batch, "hits": ref.total,
+        "launch": "one persistent launch + ordering, replayed from a CUDA graph",
+    }), flush=True)
+
+
+def run_serving(a):
+    """SERVING: Poisson arrivals (default 2000 queries/s for 10 s), m log-uniform
+    in 16..4096, k in 0..8, against the resident GENOME text; continuous
+    batching over 4 streams, admission by device memory."""
+    import torch
+    import paper_1611_06115_gb300 as pm
+    from paper_1611_06115_gb300 import serve
+    from synth import workloads
+    n = a.n
+    pats = genome_patterns()
+    host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    build_text(n, 0, host.numpy(), pats)
+    text = pm.pm_encode_text(host)
+    qs = workloads.serving_queries(rate=a.rate, duration=a.duration)
+    queries = [(q.arrival, q.pattern, q.k) for q in qs]
+    backend = serve.GpuBackend(text, slots=4)
+    # warm the kernels and the pool
+    srv = serve.Server(backend, n=n, slots=4, max_batch=32, mem_budget=32 << 30)
+    serve.run_trace(srv, queries[:20])
+    srv = serve.Server(backend, n=n, slots=4, max_batch=32, mem_budget=32 << 30)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    stats = serve.run_trace(srv, queries)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    n_cells = sum((n - len(r.pattern) + 1) * len(r.pattern) for r in srv.done)
+    stats.update({"workload": "SERVING", "n": n, "offered_rate_qps": a.rate,
+                  "arrival_seconds": a.duration, "queries": len(queries),
+                  "window_cells_per_s": n_cells / stats["span_s"],
+                  "hits": int(sum(max(r.count, 0) for r in srv.done)), "clocks": ck,
+                  "note": "latency = results on the device minus arrival; saturation when "
+                          "offered load exceeds the sustainable rate"})
+    print(json.dumps(stats), flush=True)
+
+
 if __name__ == "__main__":
     a = args_()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_ours(a)

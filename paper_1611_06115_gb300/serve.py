@@ -1,0 +1,270 @@
+"""Serving: continuous batching of pattern queries over one resident text.
+
+Queries (pattern, k) arrive over time.  The server admits queued queries into
+a batch whenever a slot (a CUDA stream) is free and the batch's projected
+device memory fits the budget; batches are issued without waiting, so those
+in different slots run concurrently on the GPU, and queries that arrive
+while others run are admitted as soon as a slot and memory free up.  A batch
+mixes queries of any m and k (one search call, one scan launch per query).
+
+Memory admission uses a per-query projection of the output size: the
+expected number of windows with at most k mismatches, from a Poisson-
+binomial model of the per-position mismatch probability (letter frequencies
+of a 41 % GC genome; a class position mismatches with the probability of
+the letters outside it), padded by a margin.  A query that still overflows
+its share is re-run alone with its exact count, which the first run reports.
+Latency is completion minus arrival; results are identical to a search of
+the query alone (the kernels are deterministic and queries never interact).
+
+The backend is pluggable: ``GpuBackend`` issues pm_search_ex calls on the
+slots' streams; tests may drive the scheduling logic with a CPU stand-in.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# letter frequencies of the synthetic genome (A, C, G, T) at 41 % GC
+LETTER_P = {"A": 0.295, "C": 0.205, "G": 0.205, "T": 0.295}
+CLASS_LETTERS = {
+    "A": "A", "C": "C", "G": "G", "T": "T", "M": "AC", "R": "AG", "W": "AT", "S": "CG",
+    "Y": "CT", "K": "GT", "V": "ACG", "H": "ACT", "D": "AGT", "B": "CGT", "N": "ACGT",
+}
+
+
+def expected_hits(pattern: str, k: int, n: int) -> float:
+    """Expected number of windows with at most k mismatches (Poisson binomial)."""
+    m = len(pattern)
+    if m > n:
+        return 0.0
+    if k >= m:
+        return float(n - m + 1)
+    # P[count = c] for c = 0..k, plus the mass beyond k (dropped)
+    dist = np.zeros(k + 1)
+    dist[0] = 1.0
+    for ch in pattern:
+        q = 1.0 - sum(LETTER_P[a] for a in CLASS_LETTERS.get(ch.upper(), ""))
+        dist[1:] = dist[1:] * (1.0 - q) + dist[:-1] * q
+        dist[0] *= (1.0 - q)
+        if dist.sum() < 1e-300:
+            break
+    return float((n - m + 1) * dist.sum())
+
+
+def capacity_for(pattern: str, k: int, n: int) -> int:
+    """Output records to reserve for one query.  The model ignores the
+    text's neighbour correlations (CpG depletion, order-2 context), which
+    move short patterns' counts by tens of percent, so the margin is wide:
+    device memory is cheaper than re-running a batch whose output did not
+    fit."""
+    e = expected_hits(pattern, k, n)
+    return int(2.0 * e + 16.0 * math.sqrt(e) + 4096)
+
+
+@dataclass
+class Request:
+    qid: int
+    pattern: str
+    k: int
+    arrival: float                  # seconds on the server clock
+    capacity: int = 0
+    start: float | None = None      # issued to the device
+    done: float | None = None       # results available
+    hits: object = None             # backend-specific (locations, mismatches)
+    count: int = -1
+    retries: int = 0
+
+    @property
+    def latency(self) -> float:
+        return (self.done - self.arrival) if self.done is not None else float("nan")
+
+
+@dataclass
+class _Flight:
+    slot: int
+    reqs: list
+    handle: object
+    nbytes: int
+
+
+class Server:
+    """Continuous-batching scheduler (see the module docstring)."""
+
+    def __init__(self, backend, n: int, slots: int = 3, max_batch: int = 64,
+                 mem_budget: int = 8 << 30, clock=time.perf_counter):
+        self.backend = backend
+        self.n = n
+        self.max_batch = max_batch
+        self.mem_budget = mem_budget
+        self.clock = clock
+        self.t0 = clock()
+        self.queue: collections.deque[Request] = collections.deque()
+        self.free_slots = list(range(slots))
+        self.flights: list[_Flight] = []
+        self.done: list[Request] = []
+        self.inflight_bytes = 0
+        self._next = 0
+        self.batches = 0
+        self.max_inflight = 0
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, pattern: str, k: int, arrival: float | None = None) -> Request:
+        r = Request(self._next, pattern, int(k), self.now() if arrival is None else arrival)
+        r.capacity = capacity_for(pattern, k, self.n)
+        self._next += 1
+        self.queue.append(r)
+        return r
+
+    def _admit(self) -> list[Request]:
+        batch, nbytes = [], 0
+        while self.queue and len(batch) < self.max_batch:
+            r = self.queue[0]
+            b = self.backend.bytes_for([r], self.n)
+            if batch and self.inflight_bytes + nbytes + b > self.mem_budget:
+                break
+            if not batch and self.flights and self.inflight_bytes + b > self.mem_budget:
+                break  # wait for memory to free up
+            batch.append(self.queue.popleft())
+            nbytes += b
+        return batch
+
+    def step(self) -> int:
+        """Harvest finished batches, then issue as many new ones as slots and
+        memory allow.  Returns the number of queries completed."""
+        finished = 0
+        still = []
+        for f in self.flights:
+            if self.backend.ready(f.handle):
+                counts, hits = self.backend.collect(f.handle, f.reqs)
+                t = self.now()
+                if any(h is None for h in hits):
+                    # the batch's output did not fit (nothing was written): run
+                    # its queries again, each with at least its exact count
+                    for r, c in reversed(list(zip(f.reqs, counts))):
+                        r.capacity, r.retries = max(r.capacity, c), r.retries + 1
+                        self.queue.appendleft(r)
+                else:
+                    for r, c, h in zip(f.reqs, counts, hits):
+                        r.count, r.hits, r.done = c, h, t
+                        self.done.append(r)
+                        finished += 1
+                self.free_slots.append(f.slot)
+                self.inflight_bytes -= f.nbytes
+            else:
+                still.append(f)
+        self.flights = still
+        while self.free_slots and self.queue:
+            batch = self._admit()
+            if not batch:
+                break
+            slot = self.free_slots.pop()
+            t = self.now()
+            for r in batch:
+                r.start = t
+            nbytes = self.backend.bytes_for(batch, self.n)
+            handle = self.backend.launch(batch, slot)
+            self.flights.append(_Flight(slot, batch, handle, nbytes))
+            self.inflight_bytes += nbytes
+            self.batches += 1
+            self.max_inflight = max(self.max_inflight, len(self.flights))
+        return finished
+
+    def idle(self) -> bool:
+        return not self.queue and not self.flights
+
+    def drain(self, poll: float = 0.0) -> None:
+        while not self.idle():
+            if self.step() == 0 and poll:
+                time.sleep(poll)
+
+
+def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
+    """Replay a list of (arrival seconds, pattern, k) on the server's clock in
+    real time, then drain.  Returns throughput and latency percentiles."""
+    queries = sorted(queries, key=lambda q: q[0])
+    i = 0
+    t_start = server.now()
+    while i < len(queries) or not server.idle():
+        now = server.now() - t_start
+        while i < len(queries) and queries[i][0] <= now:
+            a, p, k = queries[i]
+            server.submit(p, k, arrival=t_start + a)
+            i += 1
+        if server.step() == 0 and poll:
+            time.sleep(poll)
+    t_end = server.now()
+    lat = np.array([r.latency for r in server.done])
+    span = t_end - t_start
+    return {
+        "completed": len(server.done),
+        "offered_qps": len(queries) / max(queries[-1][0], 1e-9) if queries else 0.0,
+        "throughput_qps": len(server.done) / span if span > 0 else 0.0,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+        "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+        "span_s": span,
+        "batches": server.batches,
+        "max_concurrent_batches": server.max_inflight,
+        "retries": sum(r.retries for r in server.done),
+    }
+
+
+class GpuBackend:
+    """Issues each batch as one asynchronous pm_search_ex call on its slot's
+    stream (device outputs, scratch from the stream-ordered pool)."""
+
+    def __init__(self, text, slots: int = 3, copy_to_host: bool = False):
+        import torch
+        from . import api
+        self.api = api
+        self.torch = torch
+        self.text = text
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.copy_to_host = copy_to_host
+        self._compiled: dict[str, object] = {}
+
+    def _pattern(self, p: str):
+        c = self._compiled.get(p)
+        if c is None:
+            c = self.api.pm_compile_pattern(p)
+            self._compiled[p] = c
+        return c
+
+    @staticmethod
+    def bytes_for(reqs, n: int) -> int:
+        cap = sum(r.capacity for r in reqs)
+        tiles = sum((max(n - len(r.pattern) + 1, 0) + 4095) // 4096 for r in reqs)
+        return 16 * cap + 24 * tiles + 4096 * len(reqs)
+
+    def launch(self, reqs, slot: int):
+        torch = self.torch
+        st = self.streams[slot]
+        cap = sum(r.capacity for r in reqs)
+        with torch.cuda.stream(st):
+            res = self.api.pm_search_ex(self.text, [self._pattern(r.pattern) for r in reqs],
+                                        [r.k for r in reqs], capacity=cap, stream=st, sync=False)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return (res, ev, cap)
+
+    @staticmethod
+    def ready(handle) -> bool:
+        return handle[1].query()
+
+    def collect(self, handle, reqs):
+        res, ev, cap = handle
+        off = res.offsets.cpu().numpy().astype(np.uint64)
+        total = int(off[-1])
+        counts = [int(off[i + 1] - off[i]) for i in range(len(reqs))]
+        if total > cap:
+            return counts, [None] * len(reqs)
+        out = []
+        for i in range(len(reqs)):
+            seg = res.hits[int(off[i]):int(off[i + 1])]
+            out.append(seg.cpu() if self.copy_to_host else seg)
+        return counts, out

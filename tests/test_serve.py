@@ -1,0 +1,99 @@
+"""Serving scheduler (CPU): admission by memory, continuous batching, re-runs
+after an output overflow, latency accounting; results equal a solo search.
+A stand-in backend answers each batch with the oracle after a delay."""
+import time
+
+import numpy as np
+
+import oracle
+import synth
+from paper_1611_06115_gb300 import serve
+
+
+class FakeBackend:
+    """Completes a batch `delay` seconds after launch, with oracle results;
+    a batch whose output exceeds its capacity reports counts but no hits."""
+
+    def __init__(self, text, delay=0.01):
+        self.text = text
+        self.delay = delay
+        self.launched = []
+
+    @staticmethod
+    def bytes_for(reqs, n):
+        return 16 * sum(r.capacity for r in reqs) + 1000 * len(reqs)
+
+    def launch(self, reqs, slot):
+        res = [oracle.search(self.text, r.pattern, r.k, threads=1) for r in reqs]
+        self.launched.append([r.qid for r in reqs])
+        return (time.perf_counter() + self.delay, res, sum(r.capacity for r in reqs))
+
+    @staticmethod
+    def ready(h):
+        return time.perf_counter() >= h[0]
+
+    @staticmethod
+    def collect(h, reqs):
+        counts = [int(x[0].size) for x in h[1]]
+        if sum(counts) > h[2]:
+            return counts, [None] * len(reqs)
+        return counts, h[1]
+
+
+def test_expected_hits_model():
+    n = 10_000_000
+    # k >= m: every window
+    assert serve.expected_hits("ACGT", 4, n) == n - 3
+    # all-N matches everywhere
+    assert abs(serve.expected_hits("NNNN", 0, n) - (n - 3)) < 1e-6 * n
+    # one letter, k = 0: P(letter) per window
+    assert abs(serve.expected_hits("A", 0, n) - 0.295 * n) < 1e-6 * n
+    # monotone in k
+    e = [serve.expected_hits("ACGTACGTACGTACGT", k, n) for k in range(6)]
+    assert all(a <= b for a, b in zip(e, e[1:]))
+
+
+def test_continuous_batching_and_solo_equality():
+    text = synth.markov_text(200_000, seed=21)
+    rng = np.random.default_rng(21)
+    be = FakeBackend(text, delay=0.02)
+    srv = serve.Server(be, n=text.size, slots=2, max_batch=4, mem_budget=1 << 40)
+    queries = []
+    for i in range(24):
+        m = int(rng.integers(6, 60))
+        queries.append((0.005 * i, synth.random_pattern(m, m // 10, rng), int(rng.integers(0, 5))))
+    stats = serve.run_trace(srv, queries)
+    assert stats["completed"] == 24
+    assert stats["max_concurrent_batches"] == 2          # both slots busy at once
+    assert stats["batches"] >= 24 // 4                   # batches formed as queries arrived
+    for r in srv.done:
+        el, em = oracle.search(text, r.pattern, r.k)
+        assert np.array_equal(r.hits[0], el) and np.array_equal(r.hits[1], em)
+        assert r.latency >= 0.02
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+
+
+def test_memory_budget_limits_inflight():
+    text = synth.uniform_text(50_000, seed=22)
+    be = FakeBackend(text, delay=0.01)
+    one = 16 * serve.capacity_for("ACGTACGTAC", 1, text.size) + 1000
+    srv = serve.Server(be, n=text.size, slots=8, max_batch=1, mem_budget=int(2.5 * one))
+    for _ in range(10):
+        srv.submit("ACGTACGTAC", 1)
+    peak = 0
+    while not srv.idle():
+        srv.step()
+        peak = max(peak, len(srv.flights))
+        time.sleep(0.001)
+    assert peak == 2 and len(srv.done) == 10
+
+
+def test_overflow_reruns_with_exact_count():
+    text = synth.uniform_text(20_000, seed=23)
+    be = FakeBackend(text, delay=0.0)
+    srv = serve.Server(be, n=text.size, slots=1, max_batch=8, mem_budget=1 << 40)
+    r = srv.submit("ACG", 1)
+    r.capacity = 5  # far too small on purpose
+    srv.drain()
+    el, _ = oracle.search(text, "ACG", 1)
+    assert r.retries == 1 and r.count == el.size and np.array_equal(r.hits[0], el)
