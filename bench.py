@@ -197,10 +197,13 @@ def run_ours(a):
     ents = entries(pats)
     maxm = max(len(p) for p in pats)
     n = a.n
-    # rank r owns windows [r n, (r+1) n) of a world*n text: its piece carries
-    # the m-1 overlap of Sec. 2.6 (weak scaling, no collective on the data path)
-    n_local = n + (maxm - 1 if world > 1 else 0)
-    start = rank * n
+    # rank r owns window starts [r n, (r+1) n) of a world*n text: its piece
+    # carries the m-1 overlap of Sec. 2.6 (weak scaling, no collective on the
+    # data path)
+    from paper_1611_06115_gb300.shard import shard_of
+    sh = shard_of(world * n, maxm, world, rank)
+    n_local = sh.piece_len
+    start = sh.start
 
     host = torch.empty(n_local, dtype=torch.uint8, pin_memory=True)
     host_np = host.numpy()
