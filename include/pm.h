@@ -266,6 +266,24 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
                             uint32_t npat, const int32_t *k, pm_hit *hits, uint64_t capacity,
                             uint64_t *offsets, uint64_t *needed, void *stream);
 
+/* ----------------------------------------------------------- measurement */
+
+/*
+ * pm_measure_int_pipe -- throughput of one integer instruction kind on the
+ * current device, for the ALU roofline of the scan kernels.  The paper has
+ * no counterpart (its timings are of a CPU program).
+ *
+ * op        0 LOP3 (three-input logic), 1 SHF (funnel shift), 2 POPC,
+ *           3 IMAD (integer multiply-add).
+ * iters     loop trips per thread (each trip issues 8 instructions of the kind).
+ * Outputs   instructions per second over the whole GPU; the SM clock during
+ *           the run in MHz (cycle counter against the global timer); and
+ *           instructions per clock per SM (per-thread instructions: 32 per
+ *           warp instruction).  Allocates a small buffer; synchronises.
+ */
+pm_status pm_measure_int_pipe(int32_t op, uint32_t iters, double *ops_per_s, double *sm_mhz,
+                              double *ops_per_clk_per_sm);
+
 /* ---------------------------------------------------------------- status */
 
 const char *pm_status_string(pm_status status);

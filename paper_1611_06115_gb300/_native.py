@@ -75,6 +75,8 @@ SIGNATURES = {
     "pm_batch_run": (_i32, [_vp, _vp, _vp, _vp]),
     "pm_batch_capacity": (_u64, [_vp]),
     "pm_batch_free": (None, [_vp]),
+    "pm_measure_int_pipe": (_i32, [_i32, _u32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pm_status_string": (ctypes.c_char_p, [_i32]),
     "pm_last_error": (ctypes.c_char_p, []),
 }

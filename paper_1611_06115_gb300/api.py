@@ -289,3 +289,15 @@ class GraphedBatch:
     def replay(self) -> SearchResult:
         self.graph.replay()
         return self.out
+
+
+INT_OPS = ("LOP3", "SHF", "POPC", "IMAD")
+
+
+def pm_measure_int_pipe(op: int, iters: int = 20000) -> dict:
+    """Measured throughput of one integer instruction kind (see include/pm.h)."""
+    ops, mhz, per = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    N.check(N.lib().pm_measure_int_pipe(op, iters, ctypes.byref(ops), ctypes.byref(mhz),
+                                        ctypes.byref(per)), "pm_measure_int_pipe")
+    return {"op": INT_OPS[op], "ops_per_s": ops.value, "sm_mhz": mhz.value,
+            "per_clk_per_sm": per.value}

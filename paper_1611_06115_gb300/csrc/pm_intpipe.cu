@@ -1,0 +1,116 @@
+// Integer-pipe throughput microbenchmark: the peak behind the ALU roofline of
+// the scan kernels (the paper has no counterpart; it is a measurement tool).
+//
+// Each thread runs eight independent chains of one instruction kind (LOP3,
+// SHF, POPC or IMAD) written as inline PTX so that each step is exactly one
+// instruction of that kind; enough warps are launched to fill every SM.  The
+// kernel also reads the SM cycle counter and the global nanosecond timer at
+// its start and end, so the clock the GPU actually ran at is measured on the
+// device and the result can be given per SM per clock.
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_intpipe(uint32_t *out, uint32_t iters, uint32_t seed,
+                                                 unsigned long long *clk)
+{
+    uint32_t x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = seed * (threadIdx.x + 1) + 0x9e3779b9u * (j + 1);
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long c0 = 0, t0 = 0;
+    if (timer) {
+        c0 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t a = x[j], b = x[(j + 1) & 7], c = x[(j + 3) & 7];
+            uint32_t r;
+            if constexpr (OP == 0) {
+                asm volatile("lop3.b32 %0, %1, %2, %3, 0xe8;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+            } else if constexpr (OP == 1) {
+                asm volatile("shf.r.wrap.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+            } else if constexpr (OP == 2) {
+                uint32_t p;
+                asm volatile("popc.b32 %0, %1;" : "=r"(p) : "r"(b));
+                r = a ^ p;  // the XOR keeps chains dependent; count only the POPC
+            } else {
+                asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+            }
+            x[j] = r;
+        }
+    }
+    if (timer) {
+        unsigned long long c1 = clock64(), t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        clk[0] = c1 - c0;
+        clk[1] = t1 - t0;
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc ^= x[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status pm_measure_int_pipe(int32_t op, uint32_t iters, double *ops_per_s, double *sm_mhz,
+                              double *ops_per_clk_per_sm)
+{
+    if (op < 0 || op > 3 || !ops_per_s || iters == 0) {
+        set_error("pm_measure_int_pipe: op must be 0..3 (LOP3, SHF, POPC, IMAD)");
+        return PM_E_ARG;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void *fn = op == 0 ? (const void *)&k_intpipe<0>
+                   : op == 1 ? (const void *)&k_intpipe<1>
+                   : op == 2 ? (const void *)&k_intpipe<2> : (const void *)&k_intpipe<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    uint32_t *out = nullptr;
+    unsigned long long *clk = nullptr;
+    pm_status rc = cuda_status(cudaMalloc(&out, (size_t)grid * 256 * 4 + 64), "cudaMalloc");
+    if (rc) return rc;
+    clk = (unsigned long long *)((char *)out + (size_t)grid * 256 * 4);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    uint32_t seed = 12345u;
+    void *args[] = {(void *)&out, (void *)&iters, (void *)&seed, (void *)&clk};
+    rc = cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, 0), "warm-up launch");
+    if (!rc) {
+        cudaEventRecord(e0, 0);
+        rc = cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, 0), "timed launch");
+        cudaEventRecord(e1, 0);
+    }
+    float ms = 0.f;
+    unsigned long long hclk[2] = {0, 0};
+    if (!rc) rc = cuda_status(cudaEventSynchronize(e1), "synchronize");
+    if (!rc) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaMemcpy(hclk, clk, sizeof hclk, cudaMemcpyDeviceToHost);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc) return rc;
+    const double ops = (double)grid * 256.0 * iters * 8.0;
+    *ops_per_s = ops / (ms * 1e-3);
+    const double mhz = hclk[1] ? (double)hclk[0] / (double)hclk[1] * 1e3 : 0.0;
+    if (sm_mhz) *sm_mhz = mhz;
+    if (ops_per_clk_per_sm) *ops_per_clk_per_sm = mhz > 0 ? *ops_per_s / (sms * mhz * 1e6) : 0.0;
+    return PM_OK;
+}
+
+}  // extern "C"
