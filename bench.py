@@ -58,8 +58,10 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--variant", type=int, default=0)
-    ap.add_argument("--workload", choices=("genome", "batched", "serving"), default="genome",
-                    help="genome (the default line); batched and serving print their own lines")
+    ap.add_argument("--workload", choices=("genome", "batched", "serving", "profile"),
+                    default="genome",
+                    help="genome (the default line); batched and serving print their own "
+                         "lines; profile runs four single searches for an ncu capture")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: queries per second")
     return ap.parse_args()
@@ -549,10 +551,29 @@ def run_serving(a):
     print(json.dumps(stats), flush=True)
 
 
+def run_profile(a):
+    """Four single searches of the GENOME m = 128 pattern over the first n
+    symbols, one per kernel kind, for a small ncu capture:
+    (pattern-sliced, k = 4), (window-sliced, 0), (window-sliced, 4),
+    (pattern-sliced, 16)."""
+    import torch
+    import paper_1611_06115_gb300 as pm
+    pats = genome_patterns()
+    host = torch.empty(a.n, dtype=torch.uint8, pin_memory=True)
+    build_text(a.n, 0, host.numpy(), pats)
+    text = pm.pm_encode_text(host)
+    c = pm.pm_compile_pattern(pats[1])
+    for v, k in ((1, 4), (2, 0), (2, 4), (1, 16)):
+        r = pm.pm_search_ex(text, [c], [k], variant=v)
+        print(json.dumps({"variant": v, "k": k, "hits": r.total}), flush=True)
+
+
 if __name__ == "__main__":
     a = args_()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "profile":
+        run_profile(a)
     elif a.workload == "batched":
         run_batched(a)
     elif a.workload == "serving":
