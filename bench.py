@@ -45,6 +45,7 @@ MS = (32, 128, 1024)
 KS = (0, 4, 16)
 TEXT_SEED = 3
 METRIC = "window-cells/s"
+VARIANT_NAMES = {1: "pattern-sliced", 2: "window-sliced", 3: "pattern-sliced-64", 4: "all-chunks"}
 
 
 def args_():
@@ -224,6 +225,24 @@ def run_ours(a):
     handles = [cmap[p] for p, _ in ents]
     ks = [k for _, k in ents]
 
+    # the evaluation AUTO runs for each k: measured on this GPU (or read from
+    # the tuning cache) before anything is timed
+    tuned = None
+    if a.variant == 0:
+        from paper_1611_06115_gb300 import tune
+        t0 = time.perf_counter()
+        tv = tune.tune_variants(text, kmax=max(ks) + 1)
+        tuned = {"cached": tv["cached"], "seconds": time.perf_counter() - t0, "key": tv["key"]}
+    auto = pm.pm_get_auto_variants(64)
+
+    def variant_name(k):
+        v = a.variant or (auto[k] if k < 64 else pm.PM_VARIANT_ALL_CHUNKS)
+        if v == pm.PM_VARIANT_WINDOW_SLICED and k > 6:
+            v = pm.PM_VARIANT_PATTERN_SLICED
+        if (v == pm.PM_VARIANT_PATTERN_SLICED and k > 31) or (v == pm.PM_VARIANT_PATTERN_SLICED_2 and k > 63):
+            v = pm.PM_VARIANT_ALL_CHUNKS
+        return VARIANT_NAMES[v]
+
     # first search (synchronous) learns the output size and checks the planted copies
     r = pm.pm_search_ex(text, handles, ks, variant=a.variant)
     total = r.total
@@ -294,9 +313,8 @@ def run_ours(a):
     peak, peak_kind = peaks()
     # dominant kernel: the scan-kernel instance with the largest total time
     def instance(k):
-        if a.variant == 1 or (a.variant == 0 and k > 4):
-            return "k_scan<pattern-sliced>" if k <= 31 else "k_scan<pattern-sliced, all chunks>"
-        return f"k_scan<window-sliced, k={k}>"
+        name = variant_name(k)
+        return f"k_scan<{name}, k={k}>" if name == "window-sliced" else f"k_scan<{name}>"
     kinds = {}
     for e, (p, k) in enumerate(ents):
         kinds.setdefault(instance(k), []).append(e)
@@ -366,8 +384,10 @@ def run_ours(a):
             "searches_per_step": len(ents), "launch": "one scan launch per (pattern, k)",
             "l2": "inputs larger than L2 (775 MB packed text vs 129 MB L2); no flush",
             "parallelism": f"text shards with m-1 overlap x{world}",
-            "variant": {0: "auto", 1: "pattern-sliced", 2: "window-sliced"}[a.variant],
+            "variant": "auto (tuned)" if a.variant == 0 else VARIANT_NAMES[a.variant],
+            "variant_per_k": {str(k): variant_name(k) for k in sorted(set(ks))},
         },
+        "tuning": tuned,
         "text_gbs": text_gbs,
         "gbp_per_s": world * len(ents) * n / (ms / 1e3) / 1e9,
         "hits_per_step": total,
@@ -486,7 +506,14 @@ def run_batched(a):
         l, c = ref.pattern(i)
         found = dict(zip(l.tolist(), c.tolist()))
         assert all(found.get(loc) == s for loc, s in pl), f"planted copy missed, pattern {i}"
-    g = pm.GraphedBatch(pm.Batch(text, cps, ks, capacity=cap))
+    # the AUTO table for the per-pattern launches and the batch's options,
+    # both measured on this GPU (or read from the tuning cache)
+    from paper_1611_06115_gb300 import tune
+    t0 = time.perf_counter()
+    tv = tune.tune_variants(text, kmax=64)
+    tb = tune.tune_batch(text, cps, ks, cap, sample=256)
+    tune_s = time.perf_counter() - t0
+    g = pm.GraphedBatch(pm.Batch(text, cps, ks, capacity=cap, **tb["options"]))
 
     def timed(fn, reps):
         st = torch.cuda.current_stream()
@@ -505,6 +532,11 @@ def run_batched(a):
     t_batch = timed(g.replay, reps)
     out = g.out
     assert out.total == ref.total and np.array_equal(out.numpy()[0], ref.numpy()[0])
+    del g, out
+    gd = pm.GraphedBatch(pm.Batch(text, cps, ks, capacity=cap))
+    t_default = timed(gd.replay, reps)
+    assert gd.out.total == ref.total
+    del gd
     t_per = timed(lambda: pm.pm_search_ex(text, cps, ks, capacity=cap, sync=False), reps)
     n_cells = sum((n - len(p) + 1) * len(p) for p in w.patterns)
     print(json.dumps({
@@ -513,6 +545,9 @@ def run_batched(a):
         "per_pattern_launches": {"value": n_cells / t_per, "seconds": t_per},
         "batched_over_per_pattern": t_per / t_batch, "hits": ref.total,
         "launch": "one persistent launch + ordering, replayed from a CUDA graph",
+        "batch_options": tb["options"], "default_options_seconds": t_default,
+        "tuning": {"seconds": tune_s, "variants_cached": tv["cached"], "batch_cached": tb["cached"],
+                   "batch_key": tb["key"], "candidates_timed": len(tb["log"])},
     }), flush=True)
 
 

@@ -161,12 +161,24 @@ pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint
  * pm_search_ex -- pm_search with tuning and measurement options.  Results
  * are identical for every choice of options.
  *
- * variant   how the first 32 pattern positions are evaluated:
- *           PM_VARIANT_PATTERN_SLICED  one window per word, __popc counts;
- *           PM_VARIANT_WINDOW_SLICED   32 windows per word, bit-sliced
- *                                      counter (only for k <= 31; larger k
- *                                      falls back to pattern-sliced);
- *           PM_VARIANT_AUTO            chosen per pattern from k.
+ * variant   how Eq. 4 is evaluated with its early stop (Sec. 2.4-2.5):
+ *           PM_VARIANT_PATTERN_SLICED    one window per word: positions
+ *                                        0..31 by __popc, then the windows
+ *                                        still at or below k one by one
+ *                                        (k <= 31; larger k run
+ *                                        PM_VARIANT_ALL_CHUNKS);
+ *           PM_VARIANT_PATTERN_SLICED_2  the same over positions 0..63
+ *                                        (k <= 63, else ALL_CHUNKS);
+ *           PM_VARIANT_WINDOW_SLICED     32 windows per word, bit-sliced
+ *                                        counter position by position
+ *                                        (k <= 6; larger k run
+ *                                        PM_VARIANT_PATTERN_SLICED's rule);
+ *           PM_VARIANT_ALL_CHUNKS        one window per word, running
+ *                                        counts 32 positions at a time until
+ *                                        every window of a warp is past k;
+ *           PM_VARIANT_AUTO              per pattern from k, by the current
+ *                                        device's table (pm_set_auto_variants).
+ *           Any other value: PM_E_ARG.
  * grid      CTAs per scan launch; 0 means as many as the device keeps
  *           resident at once.
  * events    NULL, or 2*npat cudaEvent_t handles (created by the caller on
@@ -176,6 +188,8 @@ pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint
 #define PM_VARIANT_AUTO 0
 #define PM_VARIANT_PATTERN_SLICED 1
 #define PM_VARIANT_WINDOW_SLICED 2
+#define PM_VARIANT_PATTERN_SLICED_2 3
+#define PM_VARIANT_ALL_CHUNKS 4
 typedef struct pm_options {
     int32_t variant;
     int32_t grid;
@@ -185,6 +199,31 @@ typedef struct pm_options {
 pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
                        const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
                        uint64_t *needed, const pm_options *options, void *stream);
+
+/*
+ * pm_set_auto_variants -- the variant PM_VARIANT_AUTO runs for k = 0 ..
+ * nk-1 on the current device (an autotuner measures the candidates and
+ * installs the winners).  The paper has no counterpart: it is a choice
+ * among equivalent evaluations of Eq. 4, results are identical for every
+ * table.
+ *
+ * variant_for_k  nk PM_VARIANT_* values other than AUTO, each valid for its
+ *                k (WINDOW_SLICED needs k <= 6, PATTERN_SLICED k <= 31,
+ *                PATTERN_SLICED_2 k <= 63); read during the call only.
+ * nk             0..64; 0 restores the built-in table.  k >= nk uses the
+ *                built-in choice (k >= 64 always runs ALL_CHUNKS).  A
+ *                pattern of m <= 32 given PATTERN_SLICED_2 with k <= 31 runs
+ *                PATTERN_SLICED, which decides it exactly in half the work.
+ * Returns PM_E_ARG (table unchanged) for nk > 64, a NULL table with nk > 0,
+ * or an entry that is AUTO, unknown or not valid for its k; PM_E_CUDA if
+ * there is no current device.  Thread-safe; searches already queued keep
+ * the variants they were given.
+ *
+ * pm_get_auto_variants -- the variants PM_VARIANT_AUTO runs on the current
+ * device for k = 0 .. nk-1 (nk <= 64; PM_E_ARG otherwise), written to out.
+ */
+pm_status pm_set_auto_variants(const int32_t *variant_for_k, uint32_t nk);
+pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
 
 /* ----------------------------------------------------------------- batch */
 
@@ -201,12 +240,26 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
  *                  (cudaMalloc; about 56 bytes per unit of capacity).  The
  *                  pattern handles may be freed afterwards; the text must
  *                  outlive the batch.  Waits for its uploads.
- * options          NULL for defaults, or:
- *                    group     patterns per work item (default 8);
- *                    grid      CTAs of the persistent launch (default: as
- *                              many as the device keeps resident);
- *                    ws_max_k  largest k evaluated window-sliced (0..6;
- *                              default 4; -1 for none).
+ * options          NULL for defaults, or (0 in any field: its default):
+ *                    group      pairs per work item, rounded up to a
+ *                               multiple of 8 (default: all pairs of one
+ *                               kind of evaluation);
+ *                    grid       CTAs of the persistent launch (default: as
+ *                               many as the device keeps resident);
+ *                    tiles      warp tiles of 4096 windows per work item,
+ *                               1..4 (default 1);
+ *                    ws_below   pairs with k < ws_below are evaluated
+ *                               window-sliced, 1..7 (default 5; -1: none);
+ *                    ps1_below  other pairs with k < ps1_below are evaluated
+ *                               pattern-sliced over positions 0..31, then
+ *                               settled one window at a time, 1..32
+ *                               (default 18; -1: none);
+ *                    ps2_below  other pairs with k < ps2_below over
+ *                               positions 0..63, 1..64 (default 41; -1:
+ *                               none); the remaining pairs count every
+ *                               chunk until a warp's windows are past k.
+ *                  Out-of-range values: PM_E_ARG.  Results are identical for
+ *                  every choice of options; an autotuner picks them.
  * pm_batch_run     runs the batch into device buffers: hits (capacity
  *                  records) and offsets (npat+1; pattern p's hits are
  *                  hits[offsets[p] .. offsets[p+1]), sorted by location;
@@ -220,7 +273,10 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
 typedef struct pm_batch_options {
     int32_t group;
     int32_t grid;
-    int32_t ws_max_k;
+    int32_t tiles;
+    int32_t ws_below;
+    int32_t ps1_below;
+    int32_t ps2_below;
 } pm_batch_options;
 
 pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,

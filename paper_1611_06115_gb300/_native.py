@@ -27,6 +27,8 @@ PM_MAX_BATCH = 1 << 16
 PM_VARIANT_AUTO = 0
 PM_VARIANT_PATTERN_SLICED = 1
 PM_VARIANT_WINDOW_SLICED = 2
+PM_VARIANT_PATTERN_SLICED_2 = 3
+PM_VARIANT_ALL_CHUNKS = 4
 
 
 class NativeLibraryMissing(RuntimeError):
@@ -49,7 +51,9 @@ class pm_options(ctypes.Structure):
 
 
 class pm_batch_options(ctypes.Structure):
-    _fields_ = [("group", ctypes.c_int32), ("grid", ctypes.c_int32), ("ws_max_k", ctypes.c_int32)]
+    _fields_ = [("group", ctypes.c_int32), ("grid", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("ws_below", ctypes.c_int32), ("ps1_below", ctypes.c_int32),
+                ("ps2_below", ctypes.c_int32)]
 
 
 # Every function include/pm.h declares, with (restype, argtypes).
@@ -70,6 +74,8 @@ SIGNATURES = {
                             ctypes.POINTER(_u64), ctypes.POINTER(pm_options), _vp]),
     "pm_search_noalloc": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _vp, _u64,
                                  _vp, ctypes.POINTER(_u64), _vp]),
+    "pm_set_auto_variants": (_i32, [ctypes.POINTER(_i32), _u32]),
+    "pm_get_auto_variants": (_i32, [ctypes.POINTER(_i32), _u32]),
     "pm_batch_create": (_i32, [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_i32), _u64,
                                ctypes.c_void_p, _vp, ctypes.POINTER(_vp)]),
     "pm_batch_run": (_i32, [_vp, _vp, _vp, _vp]),

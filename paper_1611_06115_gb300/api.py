@@ -220,8 +220,12 @@ class Batch:
     captured in a CUDA graph (see ``GraphedBatch``).
     """
 
+    OPTIONS = ("group", "grid", "tiles", "ws_below", "ps1_below", "ps2_below")
+
     def __init__(self, text: Text, patterns, k, capacity: int, group: int = 0, grid: int = 0,
-                 ws_max_k: int = 0, stream=None):
+                 tiles: int = 0, ws_below: int = 0, ps1_below: int = 0, ps2_below: int = 0,
+                 stream=None):
+        """Options as pm_batch_options in include/pm.h (0: default)."""
         pats = list(patterns)
         self.npat = len(pats)
         ks = [int(k)] * self.npat if np.isscalar(k) else [int(x) for x in k]
@@ -229,7 +233,9 @@ class Batch:
             raise ValueError("one k per pattern")
         handles = (ctypes.c_void_p * max(self.npat, 1))(*[p.handle for p in pats])
         karr = (ctypes.c_int32 * max(self.npat, 1))(*ks)
-        opts = N.pm_batch_options(group, grid, ws_max_k)
+        opts = N.pm_batch_options(group, grid, tiles, ws_below, ps1_below, ps2_below)
+        self.options = dict(group=group, grid=grid, tiles=tiles, ws_below=ws_below,
+                            ps1_below=ps1_below, ps2_below=ps2_below)
         out = ctypes.c_void_p()
         N.check(N.lib().pm_batch_create(text.handle, handles, self.npat, karr, int(capacity),
                                         ctypes.cast(ctypes.byref(opts), ctypes.c_void_p),
@@ -292,6 +298,22 @@ class GraphedBatch:
 
 
 INT_OPS = ("LOP3", "SHF", "POPC", "IMAD")
+
+
+def pm_set_auto_variants(variant_for_k) -> None:
+    """Install the PM_VARIANT_AUTO table of the current device for k = 0 ..
+    len(variant_for_k) - 1 (see include/pm.h); an empty list restores the
+    built-in table."""
+    v = [int(x) for x in variant_for_k]
+    arr = (ctypes.c_int32 * max(len(v), 1))(*v)
+    N.check(N.lib().pm_set_auto_variants(arr, len(v)), "pm_set_auto_variants")
+
+
+def pm_get_auto_variants(nk: int = 64) -> list[int]:
+    """The variants PM_VARIANT_AUTO runs on the current device for k < nk."""
+    arr = (ctypes.c_int32 * max(nk, 1))()
+    N.check(N.lib().pm_get_auto_variants(arr, nk), "pm_get_auto_variants")
+    return list(arr)[:nk]
 
 
 def pm_measure_int_pipe(op: int, iters: int = 20000) -> dict:

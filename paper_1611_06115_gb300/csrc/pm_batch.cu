@@ -37,9 +37,16 @@ namespace pm {
 namespace {
 constexpr int kP = 8;  // pairs per group
 // group kinds
-constexpr uint32_t kKindShort = 0;  // pattern-sliced, k <= 31, shared shifts
-constexpr uint32_t kKindWs = 1;     // window-sliced
-constexpr uint32_t kKindLong = 2;   // pattern-sliced over all chunks, k > 31
+constexpr uint32_t kKindShort = 0;   // pattern-sliced over positions 0..31, shared shifts (k <= 31)
+constexpr uint32_t kKindWs = 1;      // window-sliced (k <= kWsMaxK)
+constexpr uint32_t kKindLong = 2;    // pattern-sliced over all chunks (any k)
+constexpr uint32_t kKindShort2 = 3;  // pattern-sliced over positions 0..63, shared shifts (k <= 63)
+// Warp tiles per work item.  The last run of tiles of an item may reach past
+// the text by up to this many tiles minus one; the text's zero padding must
+// hold their copies (each tile copies 32*G + 2 blocks).
+constexpr int kMaxTilesPerItem = 4;
+static_assert((kMaxTilesPerItem + 1) * 32 * kGroups + 2 <= kPadBlocks,
+              "the text padding covers the last run of tiles");
 }
 }  // namespace pm
 
@@ -47,18 +54,20 @@ struct pm_batch {
     int device;
     uint32_t npat;
     uint32_t ngroups;
-    uint32_t nphases;  // one per category of groups
+    uint32_t nphases;  // work-item rows: pieces of the categories of groups
     int ws_max;        // largest k evaluated window-sliced (-1: none)
     int grid;
     int key_bits;
-    uint64_t ntiles;
+    uint32_t tiles;    // warp tiles per work item
+    uint64_t ntiles;   // warp tiles of the longest window range
+    uint64_t runs;     // runs of `tiles` tiles covering them
     uint64_t capacity;
     const uint2 *planes;  // the text's planes (not owned)
     void *mem;            // one device allocation holding everything below
     pm::PatDesc *pats;
     uint32_t *order;      // pair indices, grouped
     uint32_t *gkind;      // per group: kind and number of pairs
-    uint2 *phases;        // per phase: [first group, end group)
+    uint2 *phases;        // per row: [first group, end group)
     uint4 *arena;
     pm_hit *tmp;
     pm::SegRecord *recs;
@@ -79,10 +88,12 @@ struct BatchArgs {
     const PatDesc *pats;
     const uint32_t *order;
     const uint32_t *gkind;
-    const uint2 *phases;    // [first group, end group) of each phase
+    const uint2 *phases;    // [first group, end group) of each row
     const uint4 *arena;
     uint32_t npat, ngroups;
-    uint64_t ntiles, items;  // items = phases * ntiles, phase-major
+    uint32_t tiles;         // warp tiles per item
+    uint64_t ntiles, runs;  // items = rows * runs, row-major
+    uint64_t items;
     pm_hit *tmp;
     uint64_t cap;
     unsigned long long *cursor;
@@ -129,13 +140,108 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
     }
 }
 
+// A pattern-sliced group over the first C chunks (C = 1: k <= 31, C = 2:
+// k <= 63): for each window the funnel shifts that line the text up with
+// the chunks are done once and serve all kP pairs of the group, whose masks
+// sit in shared memory.  Bytes of the multiply-add results hold
+// (4/C) * (matches + k) <= (4/C) * (64C - 1) < 256, so bit 7 of a byte is set
+// exactly when matches + k >= 32C, i.e. when the window has at most k
+// mismatches in those positions.  Windows that pass and whose pattern is
+// longer are then counted exactly (settle_staged).
+template <int C>
+__device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t pfirst,
+                                            uint32_t cnt, uint4 *sM0, uint4 *sM1, uint4 *sP,
+                                            const BatchArgs &ba)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t two = ba.pats[ba.order[pfirst]].two;
+    const uint32_t m1 = C == 1 ? two << 1 : two, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
+    if (lane < kP) {
+        // slots past cnt repeat a real pair: evaluated, never emitted
+        const uint32_t pi = __ldg(ba.order + pfirst + lane);
+        const PatDesc &dl = ba.pats[pi];
+        const uint32_t kl = (uint32_t)dl.k;
+        sM0[lane] = __ldg(ba.arena + dl.masks);
+        if (C == 2)
+            sM1[lane] = dl.nchunks > 1 ? __ldg(ba.arena + dl.masks + 1) : make_uint4(kFull, kFull, kFull, kFull);
+        sP[lane] = make_uint4(pi, kl, kl * (m24 | m16 | m8 | m1), 0u);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+        const uint2 ta = stage[32 * g + lane], tb = stage[32 * g + lane + 1];
+        const uint2 c = C == 2 ? stage[32 * g + lane + 2] : make_uint2(0u, 0u);
+        uint32_t acc[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) acc[p] = 0u;
+        // (two chunks: one step at a time, fully unrolled it would spill)
+#pragma unroll (C == 2 ? 1 : 8)
+        for (uint32_t j = 0; j < 8; ++j) {
+            uint32_t lo[4], hi[4], lo1[4], hi1[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                lo[q] = __funnelshift_r(ta.x, tb.x, 4 * j + q);
+                hi[q] = __funnelshift_r(ta.y, tb.y, 4 * j + q);
+                if (C == 2) {
+                    lo1[q] = __funnelshift_r(tb.x, c.x, 4 * j + q);
+                    hi1[q] = __funnelshift_r(tb.y, c.y, 4 * j + q);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < kP; ++p) {
+                const uint4 M0 = sM0[p];
+                uint32_t gm[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) gm[q] = __popc(class_match(lo[q], hi[q], M0));
+                if (C == 2) {
+                    const uint4 M1 = sM1[p];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) gm[q] += __popc(class_match(lo1[q], hi1[q], M1));
+                }
+                uint32_t v = mad_lo(gm[3], m24, sP[p].z);
+                v = mad_lo(gm[2], m16, v);
+                v = mad_lo(gm[1], m8, v);
+                v = mad_lo(gm[0], m1, v);
+                // window 4j + q goes to bit 8q + j
+                acc[p] |= (v >> (7 - j)) & (0x01010101u << j);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            if (p < (int)cnt) {
+                const uint32_t pi = sP[p].x, kp = sP[p].y;
+                const PatDesc &d = ba.pats[pi];
+                const uint32_t valid = valid_mask(blk, d.nwin);
+                const uint4 *M = ba.arena + d.masks;
+                uint32_t pass = acc[p] ? untranspose(acc[p]) & valid : 0u;
+                if (d.nchunks > (uint32_t)C)
+                    pass = settle_staged(pass, blk, ta, tb, stage + 32 * g + lane + 2, M, d.nchunks,
+                                         kp, ba.planes);
+                if (__any_sync(kFull, pass != 0u))
+                    emit_group(pass, blk, pi, ((unsigned long long)pi * ba.ntiles + tile) * G + g,
+                               d.nchunks, kp, M, ba);
+            }
+        }
+    }
+    __syncwarp();  // the group's shared slots are rewritten by the next group
+}
+
 // WSMAX: the largest k of the batch's window-sliced pairs (0..6).
+//
+// Each warp walks its own sequence of staged tiles: position s of the
+// sequence is tile s % T of work item first + (s / T) * stride, where an item
+// is a run of T warp tiles crossed with a row of groups (items row-major:
+// all warps work on one kind of group at a time).  The sequence is staged
+// two positions ahead into a two-stage ring; a stage is refilled once the
+// warp is done with its tile.
 template <int WSMAX>
 __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArgs ba)
 {
     __shared__ __align__(128) uint2 sbuf[kScanWarps][2][kStageBlocks];
     __shared__ __align__(8) uint64_t sbar[kScanWarps][2];
     __shared__ uint4 sM0[kScanWarps][kP];
+    __shared__ uint4 sM1[kScanWarps][kP];
     __shared__ uint4 sP[kScanWarps][kP];  // pattern-sliced group: {pair, k, k in every byte, 0}
 
     const int warp = threadIdx.x >> 5;
@@ -148,160 +254,120 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
     __syncwarp();
 
     const uint64_t stride = (uint64_t)gridDim.x * kScanWarps;
-    const uint64_t first = (uint64_t)blockIdx.x * kScanWarps + warp;
-    if (lane == 0) {
-        if (first < ba.items)
-            issue_tile(ba.planes, first % ba.ntiles, &sbuf[warp][0][0], &sbar[warp][0]);
-        if (first + stride < ba.items)
-            issue_tile(ba.planes, (first + stride) % ba.ntiles, &sbuf[warp][1][0], &sbar[warp][1]);
+    const uint32_t T = ba.tiles;
+    // sequence positions as (item, tile within its run of T)
+    auto advance = [&](uint64_t &i, uint32_t &u) {
+        if (++u == T) {
+            u = 0;
+            i += stride;
+        }
+    };
+    auto tile_of = [&](uint64_t i, uint32_t u) { return (i % ba.runs) * T + u; };
+    uint64_t ci = (uint64_t)blockIdx.x * kScanWarps + warp, pi = ci;  // consumed, next to stage
+    uint32_t cu = 0, pu = 0;
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
+        if (lane == 0 && pi < ba.items) issue_tile(ba.planes, tile_of(pi, pu), &sbuf[warp][st][0], &sbar[warp][st]);
+        advance(pi, pu);
     }
 
-    uint32_t it = 0;
-    for (uint64_t item = first; item < ba.items; item += stride, ++it) {
-        const int s = it & 1;
-        const bool ok = dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
+    for (uint64_t s = 0; ci < ba.items; ++s, advance(ci, cu)) {
+        const int st = (int)(s & 1);
+        const uint32_t par = (uint32_t)(s >> 1) & 1u;
+        const uint64_t item = ci, tile = tile_of(ci, cu);
+        const bool ok = dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
         if (__any_sync(kFull, !ok)) {
             if (lane == 0) {
                 atomicOr(ba.status, kDevTimeout);
-                dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
-                if (item + stride < ba.items)
-                    dev::mbar_wait_bounded(&sbar[warp][s ^ 1], ((it + 1) >> 1) & 1u, kWaitLimitNs);
+                // let the copies this warp still has in flight land before it leaves
+                dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
+                uint64_t ni = ci;
+                uint32_t nu = cu;
+                advance(ni, nu);
+                if (ni < ba.items)
+                    dev::mbar_wait_bounded(&sbar[warp][st ^ 1], (uint32_t)((s + 1) >> 1) & 1u, kWaitLimitNs);
             }
             return;
         }
-        // items run phase-major: all warps work on one kind of group at a time
-        const uint64_t tile = item % ba.ntiles;
-        const uint2 ph = __ldg(ba.phases + item / ba.ntiles);
-        const uint32_t g_begin = ph.x, g_end = ph.y;
-        uint2 a[G], b[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            a[g] = sbuf[warp][s][32 * g + lane];
-            b[g] = sbuf[warp][s][32 * g + lane + 1];
-        }
-        __syncwarp();
-        if (lane == 0 && item + 2 * stride < ba.items) {
-            dev::fence_proxy_async_smem();
-            issue_tile(ba.planes, (item + 2 * stride) % ba.ntiles, &sbuf[warp][s][0], &sbar[warp][s]);
-        }
-        for (uint32_t grp = g_begin; grp < g_end; ++grp) {
-        const uint32_t pfirst = grp * kP;
-        const uint32_t gk = __ldg(ba.gkind + grp);
-        const uint32_t kind = gk & 3u, cnt = gk >> 2;
+        // the tile stays staged until the item is done: evaluations read
+        // their blocks from it when they need them
+        const uint2 *stage = &sbuf[warp][st][0];
+        const uint2 ph = __ldg(ba.phases + item / ba.runs);
+        for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
+            const uint32_t pfirst = grp * kP;
+            const uint32_t gk = __ldg(ba.gkind + grp);
+            const uint32_t kind = gk & 3u, cnt = gk >> 2;
 
-        if (kind == kKindLong) {
-            // ---- k > 31: every chunk counted, one pattern at a time ----
-            for (uint32_t i = 0; i < cnt; ++i) {
-                const uint32_t p = __ldg(ba.order + pfirst + i);
-                const PatDesc d = ba.pats[p];
-                const uint4 *M = ba.arena + d.masks;
+            if (kind == kKindLong) {
+                // ---- every chunk counted, one pattern at a time ----
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    const uint32_t p = __ldg(ba.order + pfirst + i);
+                    const PatDesc d = ba.pats[p];
+                    const uint4 *M = ba.arena + d.masks;
 #pragma unroll 1
-                for (int g = 0; g < G; ++g) {
-                    const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                    const uint32_t valid = valid_mask(blk, d.nwin);
-                    const uint32_t pass = pass_multi_chunk(ba.planes, blk, M, d.nchunks, (uint32_t)d.k,
-                                                           valid, a[g], b[g]);
-                    if (__any_sync(kFull, pass != 0u))
-                        emit_group(pass, blk, p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                   d.nchunks, (uint32_t)d.k, M, ba);
-                }
-            }
-        } else if (kind == kKindShort) {
-            // ---- pattern-sliced group: shared shifts, masks from shared memory ----
-            // Bytes hold 4 * (matches + k): bit 7 of a byte is set exactly when
-            // matches + k >= 32, i.e. the window has at most k mismatches.
-            const uint32_t two = ba.pats[ba.order[pfirst]].two;
-            const uint32_t m1 = two << 1, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
-            if (lane < (int)cnt) {
-                const uint32_t pi = __ldg(ba.order + pfirst + lane);
-                const PatDesc &dl = ba.pats[pi];
-                const uint32_t kl = (uint32_t)dl.k;
-                sM0[warp][lane] = __ldg(ba.arena + dl.masks);
-                sP[warp][lane] = make_uint4(pi, kl, (kl < 32u ? kl : 0u) * (m24 | m16 | m8 | m1), 0u);
-            }
-            __syncwarp();
-#pragma unroll 1
-            for (int g = 0; g < G; ++g) {
-                const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                uint32_t acc[kP];
-#pragma unroll
-                for (int p = 0; p < kP; ++p) acc[p] = 0u;
-#pragma unroll
-                for (uint32_t j = 0; j < 8; ++j) {
-                    uint32_t lo[4], hi[4];
-#pragma unroll
-                    for (uint32_t q = 0; q < 4; ++q) {
-                        lo[q] = __funnelshift_r(a[g].x, b[g].x, 4 * j + q);
-                        hi[q] = __funnelshift_r(a[g].y, b[g].y, 4 * j + q);
-                    }
-#pragma unroll
-                    for (int p = 0; p < kP; ++p) {
-                        if (p < (int)cnt) {
-                            const uint4 M0 = sM0[warp][p];
-                            uint32_t gm[4];
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) gm[q] = __popc(class_match(lo[q], hi[q], M0));
-                            uint32_t v = mad_lo(gm[3], m24, sP[warp][p].z);
-                            v = mad_lo(gm[2], m16, v);
-                            v = mad_lo(gm[1], m8, v);
-                            v = mad_lo(gm[0], m1, v);
-                            // window 4j + q goes to bit 8q + j
-                            acc[p] |= (v >> (7 - j)) & (0x01010101u << j);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < kP; ++p) {
-                    if (p < (int)cnt) {
-                        const uint32_t pi = sP[warp][p].x, kp = sP[warp][p].y;
-                        const PatDesc &d = ba.pats[pi];
+                    for (int g = 0; g < G; ++g) {
+                        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
                         const uint32_t valid = valid_mask(blk, d.nwin);
-                        const uint4 *M = ba.arena + d.masks;
-                        uint32_t pass = acc[p] ? untranspose(acc[p]) & valid : 0u;
-                        if (d.nchunks > 1) pass = settle_lane(pass, blk, M, d.nchunks, kp, ba.planes);
+                        const uint32_t pass = pass_multi_chunk(ba.planes, blk, M, d.nchunks, (uint32_t)d.k,
+                                                               valid, stage[32 * g + lane],
+                                                               stage[32 * g + lane + 1]);
                         if (__any_sync(kFull, pass != 0u))
-                            emit_group(pass, blk, pi, ((unsigned long long)pi * ba.ntiles + tile) * G + g,
-                                       d.nchunks, kp, M, ba);
+                            emit_group(pass, blk, p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
+                                       d.nchunks, (uint32_t)d.k, M, ba);
+                    }
+                }
+            } else if (kind == kKindShort) {
+                short_group<1>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+            } else if (kind == kKindShort2) {
+                short_group<2>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+            } else {
+                // ---- window-sliced group: one pattern at a time over all groups ----
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    const uint32_t p = __ldg(ba.order + pfirst + i);
+                    const PatDesc d = ba.pats[p];
+                    uint64_t blk[G];
+                    uint32_t valid[G], pass[G];
+                    uint2 a[G], b[G];
+                    uint32_t anyv = 0;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        a[g] = stage[32 * g + lane];
+                        b[g] = stage[32 * g + lane + 1];
+                        blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+                        valid[g] = valid_mask(blk[g], d.nwin);
+                        anyv |= valid[g];
+                    }
+                    if (!__any_sync(kFull, anyv != 0u)) continue;
+                    const uint4 *list = ba.arena + d.wslist;
+                    // only the thresholds this batch uses are compiled in (instruction cache)
+                    if (d.k == 0) alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else if (WSMAX >= 1 && d.k == 1) alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else if (WSMAX >= 2 && d.k == 2) alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else if (WSMAX >= 3 && d.k == 3) alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else if (WSMAX >= 4 && d.k == 4) alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else if (WSMAX >= 5 && d.k == 5) alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    else alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    const uint4 *M = ba.arena + d.masks;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const uint32_t ps = d.nchunks > 1
+                            ? settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M,
+                                            d.nchunks, (uint32_t)d.k, ba.planes)
+                            : pass[g];
+                        if (__any_sync(kFull, ps != 0u))
+                            emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
+                                       d.nchunks, (uint32_t)d.k, M, ba);
                     }
                 }
             }
-        } else {
-            // ---- window-sliced group: one pattern at a time over all groups ----
-            for (uint32_t i = 0; i < cnt; ++i) {
-                const uint32_t p = __ldg(ba.order + pfirst + i);
-                const PatDesc d = ba.pats[p];
-                uint64_t blk[G];
-                uint32_t valid[G], pass[G];
-                uint32_t anyv = 0;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                    valid[g] = valid_mask(blk[g], d.nwin);
-                    anyv |= valid[g];
-                }
-                if (!__any_sync(kFull, anyv != 0u)) continue;
-                const uint4 *list = ba.arena + d.wslist;
-                // only the thresholds this batch uses are compiled in (instruction cache)
-                if (d.k == 0) alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else if (WSMAX >= 1 && d.k == 1) alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else if (WSMAX >= 2 && d.k == 2) alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else if (WSMAX >= 3 && d.k == 3) alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else if (WSMAX >= 4 && d.k == 4) alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else if (WSMAX >= 5 && d.k == 5) alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                else alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                const uint4 *M = ba.arena + d.masks;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const uint32_t ps = d.nchunks > 1
-                        ? settle_lane(pass[g], blk[g], M, d.nchunks, (uint32_t)d.k, ba.planes)
-                        : pass[g];
-                    if (__any_sync(kFull, ps != 0u))
-                        emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                   d.nchunks, (uint32_t)d.k, M, ba);
-                }
-            }
-        }
         }  // groups of the item
+        // the tile is done: refill its stage with sequence position s + 2
+        __syncwarp();
+        if (lane == 0 && pi < ba.items) {
+            dev::fence_proxy_async_smem();
+            issue_tile(ba.planes, tile_of(pi, pu), &sbuf[warp][st][0], &sbar[warp][st]);
+        }
+        advance(pi, pu);
     }
 }
 
@@ -367,10 +433,26 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
         return PM_E_ARG;
     }
     const pm_batch_options o = opts ? *opts : pm_batch_options{};
+    auto below_ok = [](int32_t v, int32_t hi) { return v >= -1 && v <= hi; };
+    if (o.group < 0 || o.grid < 0 || o.tiles < 0 || o.tiles > kMaxTilesPerItem ||
+        !below_ok(o.ws_below, kWsMaxK + 1) || !below_ok(o.ps1_below, 32) || !below_ok(o.ps2_below, 64)) {
+        set_error("pm_batch_create: options out of range (group %d, grid %d, tiles %d, ws_below %d, "
+                  "ps1_below %d, ps2_below %d)", o.group, o.grid, o.tiles, o.ws_below, o.ps1_below,
+                  o.ps2_below);
+        return PM_E_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
-    // in a batch the pattern-sliced groups share their text shifts, which
-    // makes them cheaper than window-sliced evaluation from k = 3 on
-    const int ws_max = o.ws_max_k > 0 ? std::min(o.ws_max_k, kWsMaxK) : (o.ws_max_k < 0 ? -1 : 2);
+    // Defaults, measured on GB300 (3.1 Gbp text, 64 pairs of m 32..1024):
+    // the window-sliced counter while few positions decide a window (k <= 4),
+    // then pattern-sliced groups with shared shifts over one chunk while the
+    // windows that survive 32 positions are rare (k <= 17), over two chunks
+    // while those surviving 64 are (k <= 40).
+    auto below = [](int32_t v, int32_t dflt) { return v == 0 ? dflt : (v < 0 ? 0 : v); };
+    const int ws_max = below(o.ws_below, 5) - 1;  // -1: none
+    const int ps1_max = below(o.ps1_below, 18) - 1;
+    const int ps2_max = below(o.ps2_below, 41) - 1;
+    const uint32_t tiles = o.tiles > 0 ? (uint32_t)o.tiles : 1u;
+    const uint32_t groups_per_row = o.group > 0 ? (uint32_t)((o.group + kP - 1) / kP) : UINT32_MAX;
 
     // descriptors and arena (host side first)
     std::vector<PatDesc> desc(npat);
@@ -399,39 +481,53 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
         d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
         d.tile0 = 0;
         d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
-        d.variant = (uint32_t)(d.k <= ws_max ? Variant::kWindowSliced : Variant::kPatternSliced);
+        // (a pattern of one chunk is decided exactly by its first 32 positions)
+        d.variant = (uint32_t)(d.k <= ws_max                                     ? Variant::kWindowSliced
+                               : d.k <= ps1_max || (d.nchunks == 1 && d.k <= 31) ? Variant::kPatternSliced
+                               : d.k <= ps2_max                                  ? Variant::kPatternSliced2
+                                                                                 : Variant::kAllChunks);
         min_m = std::min(min_m, pt->m);
     }
     if (arena.empty()) arena.push_back(make_uint4(0, 0, 0, 0));
 
-    // Categories, each one phase of the launch (all warps run one kind of
-    // evaluation at a time): window-sliced pairs with k = 0, 1, ..., then
-    // pattern-sliced pairs with k <= 31, then those with k > 31.  Within a
-    // category pairs are ordered by m and cut into groups of kP.
-    std::vector<std::vector<uint32_t>> cats(kWsMaxK + 3);
+    // Categories: window-sliced pairs with k = 0, 1, ..., then pattern-sliced
+    // pairs over one chunk, over two chunks, and over all chunks.  Within a
+    // category pairs are ordered by m and cut into groups of kP; the groups
+    // of a category are cut into rows of groups_per_row.  A work item is a
+    // row crossed with a run of `tiles` warp tiles, rows outermost, so all
+    // warps run one kind of evaluation at a time.
+    std::vector<std::vector<uint32_t>> cats(kWsMaxK + 4);
     for (uint32_t p = 0; p < npat; ++p) {
         const int32_t kp = desc[p].k;
-        size_t c;
-        if (desc[p].variant == (uint32_t)Variant::kWindowSliced) c = (size_t)kp;
-        else c = kp <= 31 ? kWsMaxK + 1 : kWsMaxK + 2;
+        const Variant v = (Variant)desc[p].variant;
+        const size_t c = v == Variant::kWindowSliced    ? (size_t)kp
+                         : v == Variant::kPatternSliced  ? kWsMaxK + 1
+                         : v == Variant::kPatternSliced2 ? kWsMaxK + 2
+                                                         : kWsMaxK + 3;
         cats[c].push_back(p);
     }
     std::vector<uint32_t> order, gkind;
     std::vector<uint2> phases;
     // gkind: bits 0-1 the kind, bits 2.. the number of real pairs (the last
-    // group of a category is padded to kP slots; padding is never evaluated)
+    // group of a category is padded to kP slots with repeats of its first
+    // pair; padding is never emitted)
     for (size_t c = 0; c < cats.size(); ++c) {
         std::vector<uint32_t> &v = cats[c];
         if (v.empty()) continue;
         std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) { return desc[x].m < desc[y].m; });
-        const uint32_t kind = c <= (size_t)kWsMaxK ? kKindWs : (c == (size_t)kWsMaxK + 1 ? kKindShort : kKindLong);
+        const uint32_t kind = c <= (size_t)kWsMaxK       ? kKindWs
+                              : c == (size_t)kWsMaxK + 1 ? kKindShort
+                              : c == (size_t)kWsMaxK + 2 ? kKindShort2
+                                                         : kKindLong;
         const uint32_t g0 = (uint32_t)gkind.size();
         for (size_t i = 0; i < v.size(); i += kP) {
             const uint32_t count = (uint32_t)std::min<size_t>(kP, v.size() - i);
             for (size_t j = i; j < i + kP; ++j) order.push_back(j < v.size() ? v[j] : v[i]);
             gkind.push_back(kind | (count << 2));
         }
-        phases.push_back(make_uint2(g0, (uint32_t)gkind.size()));
+        const uint32_t g1 = (uint32_t)gkind.size();
+        for (uint32_t r = g0; r < g1; r += std::min(groups_per_row, g1 - r))
+            phases.push_back(make_uint2(r, r + std::min(groups_per_row, g1 - r)));
     }
     const uint32_t ngroups = (uint32_t)gkind.size();
 
@@ -443,6 +539,8 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
     b->ws_max = ws_max;
     b->grid = o.grid > 0 ? o.grid : batched_grid(dev, ws_max);
     b->ntiles = min_m <= text->n ? (text->n - min_m + 1 + kTileWindows - 1) / kTileWindows : 0;
+    b->tiles = tiles;
+    b->runs = (b->ntiles + tiles - 1) / tiles;
     b->nphases = (uint32_t)phases.size();
     b->capacity = capacity;
     b->planes = text->planes;
@@ -528,11 +626,12 @@ pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *strea
         rc = cuda_status(cudaMemsetAsync(b->pat_counts, 0, b->npat * sizeof(unsigned long long), st),
                          "clear counts");
     if (rc) return rc;
-    const uint64_t items = b->ntiles * b->nphases;
+    const uint64_t items = b->runs * b->nphases;
     if (items > 0) {
-        BatchArgs ba{b->planes, b->pats, b->order, b->gkind, b->phases, b->arena, b->npat,
-                     b->ngroups, b->ntiles, items, b->tmp, b->capacity, cursor, b->recs,
-                     b->capacity, rec_cursor, b->pat_counts, status};
+        BatchArgs ba{b->planes, b->pats,  b->order,  b->gkind, b->phases,  b->arena,
+                     b->npat,   b->ngroups, b->tiles, b->ntiles, b->runs, items,
+                     b->tmp,    b->capacity, cursor,  b->recs,  b->capacity, rec_cursor,
+                     b->pat_counts, status};
         uint64_t grid = (items + kScanWarps - 1) / kScanWarps;
         if (grid > (uint64_t)b->grid) grid = (uint64_t)b->grid;
         void *args[] = {(void *)&ba};

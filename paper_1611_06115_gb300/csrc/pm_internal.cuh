@@ -86,9 +86,16 @@ constexpr uint32_t kDevTimeout = 1u;
 
 // Scan-kernel variants.
 enum class Variant : int {
-    kPatternSliced = 0,  // per window, 32 positions per word, popc
-    kWindowSliced = 1,   // per position, 32 windows per word, thermometer counter (k <= 6)
+    kPatternSliced = 0,   // per window, positions 0..31 in one word, popc; then settle (k <= 31)
+    kWindowSliced = 1,    // per position, 32 windows per word, thermometer counter (k <= 6)
+    kPatternSliced2 = 2,  // as kPatternSliced over positions 0..63 (k <= 63)
+    kAllChunks = 3,       // per window, running counts over every chunk (any k)
 };
+
+// The variant that runs when v is asked for at this k: window-sliced beyond
+// kWsMaxK becomes pattern-sliced, and a pattern-sliced form beyond its k
+// becomes kAllChunks.
+Variant resolve_variant(Variant v, int32_t k);
 
 // Launch one scan kernel for one pattern (pm_scan.cu).
 cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *arena,
@@ -98,8 +105,35 @@ cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const 
 // Number of resident scan CTAs the device runs at once (pm_scan.cu).
 int scan_grid_limit(Variant v, int32_t k, int device);
 
-// The variant chosen when the caller leaves it open.
-Variant auto_variant(const PatDesc &d);
+// The variant chosen when the caller leaves it open (the device's table, see
+// pm_set_auto_variants; already resolved for d.k).
+Variant auto_variant(const PatDesc &d, int device);
+
+// PM_VARIANT_* (not AUTO) <-> Variant.
+inline Variant variant_from_public(int32_t v)
+{
+    switch (v) {
+    case PM_VARIANT_WINDOW_SLICED: return Variant::kWindowSliced;
+    case PM_VARIANT_PATTERN_SLICED_2: return Variant::kPatternSliced2;
+    case PM_VARIANT_ALL_CHUNKS: return Variant::kAllChunks;
+    default: return Variant::kPatternSliced;
+    }
+}
+inline int32_t variant_to_public(Variant v)
+{
+    switch (v) {
+    case Variant::kWindowSliced: return PM_VARIANT_WINDOW_SLICED;
+    case Variant::kPatternSliced2: return PM_VARIANT_PATTERN_SLICED_2;
+    case Variant::kAllChunks: return PM_VARIANT_ALL_CHUNKS;
+    default: return PM_VARIANT_PATTERN_SLICED;
+    }
+}
+
+// The AUTO table: one variant per k < kAutoK for each device (pm_scan.cu).
+constexpr int kAutoK = 64;
+constexpr int kMaxAutoDevices = 64;
+pm_status set_auto_variants(int device, const Variant *table, uint32_t nk);  // nk = 0: defaults
+void get_auto_variants(int device, Variant *table);                          // kAutoK entries
 
 // Fill the run-time constants of a descriptor.
 inline void desc_constants(PatDesc &d)
@@ -168,6 +202,17 @@ namespace dev {
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// A 16-byte shared-memory load the compiler may not hoist out of a loop
+// (keeps loop-invariant masks out of registers where they would spill).
+__device__ __forceinline__ uint4 lds_u4(const uint4 *p)
+{
+    uint4 r;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "r"(smem_u32(p)));
+    return r;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)

@@ -33,6 +33,9 @@
 // Windows still at or below k after those 32 positions are counted again one
 // at a time, 32 positions per step, from position 0 until their sum exceeds k
 // or the pattern ends; that count is exact and is what a hit reports.
+#include <cstring>
+#include <mutex>
+
 #include "pm_scan_impl.cuh"
 
 namespace pm {
@@ -40,10 +43,13 @@ namespace {
 
 using namespace scan;
 
-// VARIANT: -1 pattern-sliced (k <= 31), -2 pattern-sliced over all chunks
-// (k > 31); K in 0..kWsMaxK window-sliced with threshold K.
+// VARIANT: -1 pattern-sliced over positions 0..31 (k <= 31), -3 over
+// positions 0..63 (k <= 63), -2 pattern-sliced over all chunks (any k); K in
+// 0..kWsMaxK window-sliced with threshold K.  The -2 kernel keeps 32 running
+// counts per lane in registers, so it takes twice the registers at half the
+// resident warps.
 template <int VARIANT>
-__global__ void __launch_bounds__(kScanThreads, 4)
+__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status)
@@ -100,10 +106,16 @@ __global__ void __launch_bounds__(kScanThreads, 4)
             a[g] = sbuf[warp][s][32 * g + lane];
             b[g] = sbuf[warp][s][32 * g + lane + 1];
         }
-        __syncwarp();
-        if (lane == 0 && tile + 2 * stride < d.ntiles) {
-            dev::fence_proxy_async_smem();
-            issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
+        // The pattern-sliced evaluation (k <= 31) still reads the staged tile
+        // while it settles the windows that survive the first 32 positions,
+        // so it refills the stage after the tile; the others refill it now.
+        constexpr bool kLateRefill = VARIANT == -1 || VARIANT == -3;
+        if constexpr (!kLateRefill) {
+            __syncwarp();
+            if (lane == 0 && tile + 2 * stride < d.ntiles) {
+                dev::fence_proxy_async_smem();
+                issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
+            }
         }
 
         uint64_t blk[G];
@@ -113,7 +125,14 @@ __global__ void __launch_bounds__(kScanThreads, 4)
             blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;  // windows start at 32*blk
             valid[g] = valid_mask(blk[g], d.nwin);
         }
-        tile_pass<VARIANT>(a, b, blk, valid, d, M, M0, slist, pc, planes, pass);
+        tile_pass<VARIANT>(a, b, blk, valid, d, M, M0, slist, pc, planes, &sbuf[warp][s][0], pass);
+        if constexpr (kLateRefill) {
+            __syncwarp();
+            if (lane == 0 && tile + 2 * stride < d.ntiles) {
+                dev::fence_proxy_async_smem();
+                issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
+            }
+        }
 
         // ---- hits of this warp tile, in window order (warp-aggregated atomic) ----
         uint32_t anyp = 0;
@@ -136,9 +155,11 @@ const void *kernel_ptr()
     return (const void *)&k_scan<VARIANT>;
 }
 
+// v already resolved for k
 const void *select_kernel(Variant v, int32_t k)
 {
-    if (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) {
+    switch (v) {
+    case Variant::kWindowSliced:
         switch (k) {
         case 0: return kernel_ptr<0>();
         case 1: return kernel_ptr<1>();
@@ -146,27 +167,90 @@ const void *select_kernel(Variant v, int32_t k)
         case 3: return kernel_ptr<3>();
         case 4: return kernel_ptr<4>();
         case 5: return kernel_ptr<5>();
-        case 6: return kernel_ptr<6>();
-        default: break;
+        default: return kernel_ptr<6>();
         }
+    case Variant::kPatternSliced: return kernel_ptr<-1>();
+    case Variant::kPatternSliced2: return kernel_ptr<-3>();
+    default: return kernel_ptr<-2>();
     }
-    return k > 31 ? kernel_ptr<-2>() : kernel_ptr<-1>();
+}
+
+// Per device, the variant PM_VARIANT_AUTO uses for k < kAutoK (-1: the
+// built-in choice); larger k always run kAllChunks.
+std::mutex g_auto_mu;
+int8_t g_auto[kMaxAutoDevices][kAutoK];
+bool g_auto_init = false;
+
+Variant default_variant(int32_t k)
+{
+    // measured on GB300 over a 3.1 Gbp text (m = 128 .. 10^4): the
+    // window-sliced counter wins while few positions decide a window, one
+    // pattern-sliced chunk while the windows that survive it are rare, two
+    // chunks while those surviving 64 positions are rare
+    if (k <= 4) return Variant::kWindowSliced;
+    if (k <= 17) return Variant::kPatternSliced;
+    if (k <= 40) return Variant::kPatternSliced2;
+    return Variant::kAllChunks;
 }
 
 }  // namespace
 
-Variant auto_variant(const PatDesc &d)
+Variant resolve_variant(Variant v, int32_t k)
 {
-    // window-sliced wins while few positions decide a window (small k)
-    return d.k <= 4 ? Variant::kWindowSliced : Variant::kPatternSliced;
+    switch (v) {
+    case Variant::kWindowSliced:
+        return k >= 0 && k <= kWsMaxK ? v : resolve_variant(Variant::kPatternSliced, k);
+    case Variant::kPatternSliced: return k <= 31 ? v : Variant::kAllChunks;
+    case Variant::kPatternSliced2: return k <= 63 ? v : Variant::kAllChunks;
+    default: return Variant::kAllChunks;
+    }
+}
+
+Variant auto_variant(const PatDesc &d, int device)
+{
+    if (d.k < 0 || d.k >= kAutoK) return Variant::kAllChunks;
+    int v = -1;
+    if (device >= 0 && device < kMaxAutoDevices) {
+        std::lock_guard<std::mutex> lk(g_auto_mu);
+        if (g_auto_init) v = g_auto[device][d.k];
+    }
+    Variant r = resolve_variant(v < 0 ? default_variant(d.k) : (Variant)v, d.k);
+    // a pattern of one chunk is decided exactly by its first 32 positions
+    if (r == Variant::kPatternSliced2 && d.nchunks == 1 && d.k <= 31) r = Variant::kPatternSliced;
+    return r;
+}
+
+pm_status set_auto_variants(int device, const Variant *table, uint32_t nk)
+{
+    if (device < 0 || device >= kMaxAutoDevices) return PM_E_ARG;
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    if (!g_auto_init) {
+        std::memset(g_auto, -1, sizeof(g_auto));
+        g_auto_init = true;
+    }
+    for (int k = 0; k < kAutoK; ++k)
+        g_auto[device][k] = (uint32_t)k < nk ? (int8_t)table[k] : (int8_t)-1;
+    return PM_OK;
+}
+
+void get_auto_variants(int device, Variant *table)
+{
+    for (int k = 0; k < kAutoK; ++k) {
+        PatDesc d{};
+        d.k = k;
+        table[k] = auto_variant(d, device);
+    }
 }
 
 int scan_grid_limit(Variant v, int32_t k, int device)
 {
-    static int cache[64][kWsMaxK + 3] = {};
+    static int cache[64][kWsMaxK + 4] = {};
     if (device < 0 || device >= 64) return 0;
-    const int slot = (v == Variant::kWindowSliced && k >= 0 && k <= kWsMaxK) ? k
-                     : (k > 31 ? kWsMaxK + 2 : kWsMaxK + 1);
+    v = resolve_variant(v, k);
+    const int slot = v == Variant::kWindowSliced     ? k
+                     : v == Variant::kPatternSliced  ? kWsMaxK + 1
+                     : v == Variant::kPatternSliced2 ? kWsMaxK + 2
+                                                     : kWsMaxK + 3;
     if (cache[device][slot]) return cache[device][slot];
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -184,7 +268,7 @@ cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const 
     const uint64_t ctas_needed = (d.ntiles + kScanWarps - 1) / kScanWarps;
     if ((uint64_t)grid > ctas_needed) grid = (int)ctas_needed;
     if (grid < 1) grid = 1;
-    const void *fn = select_kernel(v, d.k);
+    const void *fn = select_kernel(resolve_variant(v, d.k), d.k);
     PatDesc dd = d;
     void *args[] = {(void *)&planes, (void *)&dd, (void *)&arena, (void *)&table,
                     (void *)&tmp,    (void *)&cap, (void *)&cursor, (void *)&status};
@@ -192,3 +276,44 @@ cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const 
 }
 
 }  // namespace pm
+
+extern "C" {
+
+pm_status pm_set_auto_variants(const int32_t *variant_for_k, uint32_t nk)
+{
+    if (nk > (uint32_t)pm::kAutoK || (nk > 0 && !variant_for_k)) {
+        pm::set_error("pm_set_auto_variants: nk = %u (0..%d) or NULL table", nk, pm::kAutoK);
+        return PM_E_ARG;
+    }
+    pm::Variant t[pm::kAutoK];
+    for (uint32_t k = 0; k < nk; ++k) {
+        const int32_t v = variant_for_k[k];
+        if (v < PM_VARIANT_PATTERN_SLICED || v > PM_VARIANT_ALL_CHUNKS ||
+            pm::resolve_variant(pm::variant_from_public(v), (int32_t)k) != pm::variant_from_public(v)) {
+            pm::set_error("pm_set_auto_variants: variant %d is not valid for k = %u", v, k);
+            return PM_E_ARG;
+        }
+        t[k] = pm::variant_from_public(v);
+    }
+    int dev = 0;
+    pm_status rc = pm::cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    return pm::set_auto_variants(dev, t, nk);
+}
+
+pm_status pm_get_auto_variants(int32_t *out, uint32_t nk)
+{
+    if (nk > (uint32_t)pm::kAutoK || (nk > 0 && !out)) {
+        pm::set_error("pm_get_auto_variants: nk = %u (0..%d) or NULL output", nk, pm::kAutoK);
+        return PM_E_ARG;
+    }
+    int dev = 0;
+    pm_status rc = pm::cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    pm::Variant t[pm::kAutoK];
+    pm::get_auto_variants(dev, t);
+    for (uint32_t k = 0; k < nk; ++k) out[k] = pm::variant_to_public(t[k]);
+    return PM_OK;
+}
+
+}  // extern "C"

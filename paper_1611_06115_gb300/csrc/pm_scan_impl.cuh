@@ -52,13 +52,21 @@ __device__ __forceinline__ uint32_t untranspose(uint32_t t)
     return r;
 }
 
-// Pattern-sliced first chunk for one lane's 32 windows; transposed pass mask
-// of the windows with at most k mismatches in positions 0..31 (k <= 31).
-// k4 = k in every byte; one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
-__device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint4 M0, uint32_t k4,
-                                                        uint32_t one, uint32_t m8, uint32_t m16,
-                                                        uint32_t m24)
+// Pattern-sliced test of the first C chunks (C = 1 or 2) for one lane's 32
+// windows; transposed pass mask of the windows with at most k mismatches in
+// positions 0..32C-1 (k <= 32C-1).  Blocks blk, blk+1 (and blk+2 for C = 2)
+// are a, b, c; M0, M1 the masks of chunks 0 and 1.  Every byte of the
+// multiply-add result holds matches + k, below 2^(5+C) so bytes never
+// carry: its bit 4+C is set exactly when matches + k >= 32C,
+// i.e. when the window has at most k mismatches.  k4 = k in every byte;
+// one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
+template <int C>
+__device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint2 c, uint4 M0,
+                                                        uint4 M1, uint32_t k4, uint32_t one,
+                                                        uint32_t m8, uint32_t m16, uint32_t m24)
 {
+    static_assert(C == 1 || C == 2, "one or two chunks");
+    constexpr int kBit = 4 + C;
     uint32_t pass = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -66,16 +74,16 @@ __device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint4 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int w = 4 * j + q;
-            const uint32_t lo = __funnelshift_r(a.x, b.x, w);
-            const uint32_t hi = __funnelshift_r(a.y, b.y, w);
-            g[q] = __popc(class_match(lo, hi, M0));
+            g[q] = __popc(class_match(__funnelshift_r(a.x, b.x, w), __funnelshift_r(a.y, b.y, w), M0));
+            if constexpr (C == 2)
+                g[q] += __popc(class_match(__funnelshift_r(b.x, c.x, w), __funnelshift_r(b.y, c.y, w), M1));
         }
         uint32_t v = mad_lo(g[3], m24, k4);
         v = mad_lo(g[2], m16, v);
         v = mad_lo(g[1], m8, v);
         v = mad_lo(g[0], one, v);
-        // bit 5 of byte q: g[q] + k >= 32; move bits 5, 13, 21, 29 to 8q + j
-        const uint32_t s = j <= 5 ? v >> (5 - j) : v << (j - 5);
+        // bit kBit of byte q: g[q] + k >= 32C; move bits 8q + kBit to 8q + j
+        const uint32_t s = j <= kBit ? v >> (kBit - j) : v << (j - kBit);
         pass |= s & (0x01010101u << j);
     }
     return pass;
@@ -235,7 +243,33 @@ __device__ __forceinline__ uint32_t settle_lane(uint32_t pass, uint64_t blk,
     return pass;
 }
 
-// Run-time constants of the pattern-sliced byte test for one k.
+// settle_lane for a lane whose blocks blk and blk+1 are in registers (t0, t1)
+// and whose block blk+2 is still staged in shared memory (s_next): chunks 0
+// and 1 need no load through L1/L2, deeper chunks (rarely reached while k is
+// below the expected mismatches of 64 positions) use window_count_from.
+__device__ __forceinline__ uint32_t settle_staged(uint32_t pass, uint64_t blk, uint2 t0, uint2 t1,
+                                                 const uint2 *s_next, const uint4 *__restrict__ M,
+                                                 uint32_t nchunks, uint32_t k,
+                                                 const uint2 *__restrict__ planes)
+{
+    if (!pass) return 0u;
+    const uint4 M0 = __ldg(M), M1 = __ldg(M + 1);
+    const uint2 t2 = *s_next;
+    uint32_t sv = pass;
+    while (sv) {
+        const uint32_t w = __ffs(sv) - 1;
+        sv &= sv - 1;
+        uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), M0));
+        if (c <= k)
+            c += __popc(~class_match(__funnelshift_r(t1.x, t2.x, w), __funnelshift_r(t1.y, t2.y, w), M1));
+        if (c <= k && nchunks > 2) c = window_count_from(planes, blk, w, M, 2, nchunks, c, k);
+        if (c > k) pass &= ~(1u << w);
+    }
+    return pass;
+}
+
+// Run-time constants of the pattern-sliced byte test for one k (k <= 63;
+// the kernels use it only where k < 32C).
 struct PsConst {
     uint32_t one, m8, m16, m24, k4;
 };
@@ -247,20 +281,21 @@ __device__ __forceinline__ PsConst ps_const(uint32_t two, uint32_t k)
     c.m8 = c.one << 8;
     c.m16 = c.one << 16;
     c.m24 = c.one << 24;
-    c.k4 = (k < 32u ? k : 0u) * (c.m24 | c.m16 | c.m8 | c.one);
+    c.k4 = (k < 64u ? k : 0u) * (c.m24 | c.m16 | c.m8 | c.one);
     return c;
 }
 
 // The windows of one warp tile that hold the pattern with at most k
 // mismatches: pass[g] bit w for window 32*blk[g] + w.  VARIANT as in k_scan;
-// list (window-sliced only) is the pattern's position list in shared memory.
+// list (window-sliced only) is the pattern's position list in shared memory;
+// stage (pattern-sliced, -1 and -3) is the tile still staged in shared memory.
 template <int VARIANT>
 __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[G],
                                           const uint64_t (&blk)[G], const uint32_t (&valid)[G],
                                           const PatDesc &d, const uint4 *__restrict__ M,
                                           uint4 M0, const uint4 *__restrict__ list,
                                           const PsConst &pc, const uint2 *__restrict__ planes,
-                                          uint32_t (&pass)[G])
+                                          const uint2 *stage, uint32_t (&pass)[G])
 {
     const uint32_t k = (uint32_t)d.k;
     if constexpr (VARIANT >= 0) {
@@ -272,20 +307,34 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
             pass[g] = pass_multi_chunk(planes, blk[g], M, d.nchunks, k, valid[g], a[g], b[g]);
         return;
     } else {
+        // -1: one chunk; -3: two chunks (chunk 1 of a pattern with m <= 32
+        // reads as all ones: every position past m matches)
+        constexpr int C = VARIANT == -3 ? 2 : 1;
+        const int lane = threadIdx.x & 31;
+        const uint4 M1 = (C == 2 && d.nchunks > 1) ? __ldg(M + 1) : make_uint4(kFull, kFull, kFull, kFull);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             uint32_t t = 0u;
-            if (valid[g])
-                t = untranspose(pass_pattern_sliced(a[g], b[g], M0, pc.k4, pc.one, pc.m8, pc.m16,
-                                                    pc.m24)) & valid[g];
+            if (valid[g]) {
+                const uint2 c = C == 2 ? stage[32 * g + lane + 2] : make_uint2(0u, 0u);
+                t = untranspose(pass_pattern_sliced<C>(a[g], b[g], c, M0, M1, pc.k4, pc.one, pc.m8,
+                                                       pc.m16, pc.m24)) & valid[g];
+            }
             pass[g] = t;
         }
     }
     // Both evaluations are exact for m <= 32.  Longer patterns: count every
     // remaining window exactly and drop those past k.
     if (d.nchunks > 1) {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int g = 0; g < G; ++g) pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
+        for (int g = 0; g < G; ++g) {
+            if constexpr (VARIANT == -1 || VARIANT == -3)
+                pass[g] = settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M,
+                                        d.nchunks, k, planes);
+            else
+                pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
+        }
     }
 }
 

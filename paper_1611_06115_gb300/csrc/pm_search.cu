@@ -93,6 +93,10 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
         }
     }
     const pm_options o = opts ? *opts : pm_options{};
+    if (o.variant < PM_VARIANT_AUTO || o.variant > PM_VARIANT_ALL_CHUNKS) {
+        set_error("pm_search: unknown variant %d", o.variant);
+        return PM_E_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -198,10 +202,9 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
 
     // ---- one scan launch per pattern ----
     for (uint32_t p = 0; !rc && p < npat; ++p) {
-        Variant v = auto_variant(desc[p]);
-        if (o.variant == PM_VARIANT_PATTERN_SLICED) v = Variant::kPatternSliced;
-        else if (o.variant == PM_VARIANT_WINDOW_SLICED) v = Variant::kWindowSliced;
-        if (v == Variant::kWindowSliced && desc[p].k > kWsMaxK) v = Variant::kPatternSliced;
+        const Variant v = o.variant == PM_VARIANT_AUTO
+                              ? auto_variant(desc[p], dev)
+                              : resolve_variant(variant_from_public(o.variant), desc[p].k);
         const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, desc[p].k, dev);
         if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p], st);
         rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,

@@ -36,23 +36,44 @@ CLASS_LETTERS = {
 }
 
 
+def _binomial_head(c: int, q: float, k: int) -> list[float]:
+    """P[Binomial(c, q) = i] for i = 0..k (log space, so (1-q)^c may underflow
+    to 0 without a NaN)."""
+    if q <= 0.0:
+        return [1.0] + [0.0] * k
+    if q >= 1.0:
+        return [1.0 if i == c else 0.0 for i in range(k + 1)]
+    lq, lp = math.log(q), math.log1p(-q)
+    out = []
+    for i in range(k + 1):
+        if i > c:
+            out.append(0.0)
+            continue
+        lg = math.lgamma(c + 1) - math.lgamma(i + 1) - math.lgamma(c - i + 1)
+        out.append(math.exp(lg + i * lq + (c - i) * lp))
+    return out
+
+
 def expected_hits(pattern: str, k: int, n: int) -> float:
-    """Expected number of windows with at most k mismatches (Poisson binomial)."""
+    """Expected number of windows with at most k mismatches.
+
+    The count of a window is a sum of independent per-position mismatch
+    indicators (a Poisson binomial); positions of the same class share one
+    probability, so the distribution's head (counts 0..k) is the truncated
+    convolution of one binomial per class present.  Costs O(classes * k^2)
+    instead of O(m * k): it runs once per submitted query, on the host thread
+    that also feeds the GPU."""
     m = len(pattern)
     if m > n:
         return 0.0
     if k >= m:
         return float(n - m + 1)
-    # P[count = c] for c = 0..k, plus the mass beyond k (dropped)
-    dist = np.zeros(k + 1)
-    dist[0] = 1.0
-    for ch in pattern:
-        q = 1.0 - sum(LETTER_P[a] for a in CLASS_LETTERS.get(ch.upper(), ""))
-        dist[1:] = dist[1:] * (1.0 - q) + dist[:-1] * q
-        dist[0] *= (1.0 - q)
-        if dist.sum() < 1e-300:
-            break
-    return float((n - m + 1) * dist.sum())
+    dist = [1.0] + [0.0] * k
+    for ch, c in collections.Counter(pattern.upper()).items():
+        q = 1.0 - sum(LETTER_P[a] for a in CLASS_LETTERS.get(ch, ""))
+        b = _binomial_head(c, q, k)
+        dist = [sum(dist[j] * b[i - j] for j in range(i + 1)) for i in range(k + 1)]
+    return float((n - m + 1) * sum(dist))
 
 
 def capacity_for(pattern: str, k: int, n: int) -> int:

@@ -46,8 +46,10 @@ def test_batch_mixed_patterns_vs_oracle(pm):
     t = pm.pm_encode_text(text)
     cps = [pm.pm_compile_pattern(p) for p in pats]
     cap = pm.pm_search(t, cps, ks).total + 10
-    for group, ws in ((8, 0), (1, -1), (5, 6)):
-        b = pm.Batch(t, cps, ks, capacity=cap, group=group, ws_max_k=ws)
+    for opts in (dict(), dict(group=1, ws_below=-1), dict(group=5, ws_below=7, tiles=3),
+                 dict(ws_below=1, ps1_below=-1, tiles=4), dict(ps1_below=5, ps2_below=64, tiles=2),
+                 dict(ws_below=-1, ps1_below=-1, ps2_below=-1, group=16)):
+        b = pm.Batch(t, cps, ks, capacity=cap, **opts)
         res = b.run()
         torch.cuda.synchronize()
         assert res.total <= cap
@@ -130,3 +132,33 @@ def test_batched_recipe_reduced(pm):
         found = dict(zip(seg[:, 0].tolist(), seg[:, 1].tolist()))
         for loc, s in w.planted[i]:
             assert found.get(loc) == s
+
+
+def test_autotuner_on_device(pm, tmp_path):
+    """The tuner measures on the device, caches, installs a valid AUTO table
+    and batch options; searches under them give the oracle's hits."""
+    import torch
+    from paper_1611_06115_gb300 import tune
+    rng = np.random.default_rng(61)
+    text = synth.markov_text(4 * 4096 * 32 + 17, seed=61)
+    t = pm.pm_encode_text(text)
+    path = str(tmp_path / "tune.json")
+    builtin = pm.pm_get_auto_variants()
+    try:
+        r = tune.tune_variants(t, kmax=24, ms=(40, 200), reps=1, cache=path)
+        assert not r["cached"] and pm.pm_get_auto_variants(24) == r["table"]
+        assert tune.tune_variants(t, kmax=24, cache=path)["cached"]
+        pats = [synth.random_pattern(m, m // 10, rng) for m in (12, 40, 64, 100, 300)] * 4
+        ks = [0, 3, 6, 12, 19, 25, 40, 2, 5, 8, 17, 30, 1, 4, 9, 21, 33, 45, 0, 16]
+        cps = [pm.pm_compile_pattern(p) for p in pats]
+        ref = pm.pm_search(t, cps, ks)
+        check_against_oracle(ref, text, pats, ks)
+        b = tune.tune_batch(t, cps, ks, ref.total + 10, sample=8, reps=1, cache=path)
+        assert not b["cached"] and len(b["log"]) > 5
+        batch = pm.Batch(t, cps, ks, capacity=ref.total + 10, **b["options"])
+        res = batch.run()
+        torch.cuda.synchronize()
+        check_against_oracle(res, text, pats, ks)
+    finally:
+        pm.pm_set_auto_variants([])
+    assert pm.pm_get_auto_variants() == builtin

@@ -19,7 +19,9 @@ pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 SYMBOLS = "ACGTMRWSYKVHDBN-"
-VARIANTS = (0, 1, 2)  # auto, pattern-sliced, window-sliced
+# auto, pattern-sliced (32 positions), window-sliced, pattern-sliced (64
+# positions), every chunk
+VARIANTS = (0, 1, 2, 3, 4)
 
 
 @pytest.fixture(scope="module")
@@ -250,3 +252,54 @@ def test_large_patterns_reduced(pm):
         got = gpu_hits(pm, w.text, [p] * 3, [0, 100, 1000])
         for (l, c), k in zip(got, (0, 100, 1000)):
             same((l, c), oracle.search(w.text, p, k))
+
+
+@pytest.mark.parametrize("variant", (1, 3, 4))
+def test_mid_k_many_survivors(pm, variant):
+    """k from 17 to 63 on patterns of two to ten chunks: many windows survive
+    the first 32 (or 64) positions and are settled one by one, or counted by
+    every chunk; all forms give the oracle's hits."""
+    rng = np.random.default_rng(40 + variant)
+    n = 3 * 4096 * 32 + 321
+    text = synth.markov_text(n, seed=31)
+    pats, ks = [], []
+    for m in (40, 64, 65, 96, 130, 300):
+        for k in (17, 20, 24, 31, 40, 63):
+            pats.append(synth.random_pattern(m, m // 10, rng))
+            ks.append(k)
+    got = gpu_hits(pm, text, pats, ks, variant=variant)
+    for p, k, g in zip(pats, ks, got):
+        same(g, oracle.search(text, p, k))
+
+
+def test_auto_variant_table(pm):
+    """pm_set_auto_variants: any valid table gives the same hits; invalid
+    tables are rejected and leave the table unchanged; [] restores it."""
+    rng = np.random.default_rng(77)
+    text = synth.markov_text(2 * 4096 * 32 + 55, seed=8)
+    pats = [synth.random_pattern(m, m // 10, rng) for m in (20, 70, 200)]
+    ks = [0, 5, 18, 33]
+    exp = [[oracle.search(text, p, k) for k in ks] for p in pats]
+    builtin = pm.pm_get_auto_variants()
+    assert len(builtin) == 64
+    tables = ([pm.PM_VARIANT_ALL_CHUNKS] * 64,
+              [pm.PM_VARIANT_WINDOW_SLICED if k <= 6 else pm.PM_VARIANT_PATTERN_SLICED_2 for k in range(64)],
+              [pm.PM_VARIANT_PATTERN_SLICED] * 20)
+    try:
+        for table in tables:
+            pm.pm_set_auto_variants(table)
+            assert pm.pm_get_auto_variants(len(table)) == list(table)
+            for p, e in zip(pats, exp):
+                got = gpu_hits(pm, text, [p] * len(ks), ks)
+                for g, x in zip(got, e):
+                    same(g, x)
+        before = pm.pm_get_auto_variants()
+        for bad in ([pm.PM_VARIANT_AUTO], [pm.PM_VARIANT_WINDOW_SLICED] * 8, [pm.PM_VARIANT_PATTERN_SLICED] * 33,
+                    [7], [pm.PM_VARIANT_ALL_CHUNKS] * 65):
+            with pytest.raises(pm.PmError):
+                pm.pm_set_auto_variants(bad)
+            assert pm.pm_get_auto_variants() == before
+    finally:
+        pm.pm_set_auto_variants([])
+    assert pm.pm_get_auto_variants() == builtin
+

@@ -53,6 +53,45 @@ def test_expected_hits_model():
     assert all(a <= b for a, b in zip(e, e[1:]))
 
 
+def test_expected_hits_against_enumeration():
+    """The grouped-binomial form equals the probability mass of all texts of
+    length m with at most k mismatches, enumerated letter by letter."""
+    import itertools
+    letters = "ACGT"
+    n = 1000
+    for pat in ("ACG", "RYKN", "AAWSB", "TTTTT", "HDVBMM"):
+        m = len(pat)
+        for k in range(m + 1):
+            mass = 0.0
+            for t in itertools.product(letters, repeat=m):
+                mm = sum(1 for p, c in zip(pat, t) if c not in serve.CLASS_LETTERS[p])
+                if mm <= k:
+                    pr = 1.0
+                    for c in t:
+                        pr *= serve.LETTER_P[c]
+                    mass += pr
+            assert abs(serve.expected_hits(pat, k, n) - (n - m + 1) * mass) < 1e-9 * n, (pat, k)
+
+
+def test_expected_hits_long_pattern_matches_position_recursion():
+    """For a long pattern with classes, the grouped form agrees with the
+    position-by-position Poisson-binomial recursion."""
+    rng = np.random.default_rng(5)
+    alphabet = list(serve.CLASS_LETTERS)
+    pat = "".join(rng.choice(alphabet, size=300))
+    n = 10_000_000
+    for k in (0, 3, 40, 120, 200):
+        dist = np.zeros(k + 1)
+        dist[0] = 1.0
+        for ch in pat:
+            q = 1.0 - sum(serve.LETTER_P[a] for a in serve.CLASS_LETTERS[ch])
+            dist[1:] = dist[1:] * (1.0 - q) + dist[:-1] * q
+            dist[0] *= 1.0 - q
+        want = (n - len(pat) + 1) * dist.sum()
+        got = serve.expected_hits(pat, k, n)
+        assert abs(got - want) <= 1e-9 * max(want, 1.0), (k, got, want)
+
+
 def test_continuous_batching_and_solo_equality():
     text = synth.markov_text(200_000, seed=21)
     rng = np.random.default_rng(21)
