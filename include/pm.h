@@ -81,6 +81,11 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
 
 /* Number of symbols of an encoded text. */
 uint64_t pm_text_length(const pm_text *text);
+/* How many A, C, G, T (counts[0..3], Table 1 order) the text holds; they
+ * sum to its length.  Counted while coding (pm_encode_text); the search uses
+ * them to order the positions it tests first (fewest matches first), which
+ * changes no result.  PM_E_ARG for NULL arguments. */
+pm_status pm_text_letter_counts(const pm_text *text, uint64_t counts[4]);
 
 /* Device address and size in bytes of the coded planes (read-only view for
  * callers that want to inspect the layout); either out pointer may be NULL. */

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pm_text_length": (_u64, [_vp]),
     "pm_text_device_planes": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),
     "pm_text_free": (None, [_vp]),
+    "pm_text_letter_counts": (_i32, [_vp, ctypes.POINTER(_u64)]),
     "pm_compile_pattern": (_i32, [ctypes.c_char_p, _u32, ctypes.POINTER(_vp)]),
     "pm_pattern_length": (_u32, [_vp]),
     "pm_pattern_unknown": (_u32, [_vp]),

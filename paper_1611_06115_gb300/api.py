@@ -56,6 +56,12 @@ class Text:
                 "pm_text_device_planes")
         return int(p.value or 0), int(b.value)
 
+    def letter_counts(self) -> list[int]:
+        """How many A, C, G, T the text holds (pm_text_letter_counts)."""
+        arr = (ctypes.c_uint64 * 4)()
+        N.check(N.lib().pm_text_letter_counts(self._h, arr), "pm_text_letter_counts")
+        return list(arr)
+
     def free(self):
         if self._h is not None and self._h.value:
             N.lib().pm_text_free(self._h)

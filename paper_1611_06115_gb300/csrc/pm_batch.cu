@@ -466,7 +466,9 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
             const uint64_t mo = arena.size();
             arena.insert(arena.end(), pt->masks, pt->masks + pt->nchunks);
             const uint64_t lo = arena.size();
-            arena.insert(arena.end(), pt->wslist, pt->wslist + pt->n_single + 2 * pt->n_general);
+            uint4 list[64];  // at most 2 entries per position of the first 32
+            ordered_wslist(pt, text, list);
+            arena.insert(arena.end(), list, list + pt->n_single + 2 * pt->n_general);
             it = where.emplace(pt, std::make_pair(mo, lo)).first;
         }
         PatDesc &d = desc[p];

@@ -17,13 +17,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "pm.h"
 
 struct pm_text {
-    uint64_t n;        // symbols
-    uint64_t nblocks;  // allocated blocks, padding included
-    uint2 *planes;     // device
+    uint64_t n;         // symbols
+    uint64_t nblocks;   // allocated blocks, padding included
+    uint2 *planes;      // device
     int device;
+    uint64_t count[4];  // how many A, C, G, T the text holds (Table 1 order)
 };
 
 struct pm_pattern {
@@ -42,6 +45,45 @@ struct pm_pattern {
 };
 
 namespace pm {
+
+// The window-sliced list of p (see pm_pattern) reordered for text t so that
+// windows die as early as possible (the early stop of Sec. 2.4 then ends the
+// scan sooner; the sum of Eq. 4 does not depend on the order): one-letter
+// entries by increasing frequency of their letter in t, then the class
+// entries by increasing frequency of their letters.  Stable; out receives
+// n_single + 2 * n_general entries.
+inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
+{
+    const uint32_t ns = p->n_single, ng = p->n_general;
+    uint32_t idx[64];
+    uint64_t key[64];
+    for (uint32_t i = 0; i < ns; ++i) {
+        const uint4 e = p->wslist[i];
+        idx[i] = i;
+        key[i] = t->count[(e.y & 1u) | ((e.z & 1u) << 1)];
+    }
+    for (uint32_t i = 0; i < ng; ++i) {
+        const uint4 mem = p->wslist[ns + 2 * i + 1];
+        idx[ns + i] = i;
+        key[ns + i] = (mem.x ? t->count[0] : 0) + (mem.y ? t->count[1] : 0) +
+                      (mem.z ? t->count[2] : 0) + (mem.w ? t->count[3] : 0);
+    }
+    // insertion sorts (at most 32 entries each), stable
+    auto sort_range = [&](uint32_t lo, uint32_t hi) {
+        for (uint32_t i = lo + 1; i < hi; ++i)
+            for (uint32_t j = i; j > lo && key[j] < key[j - 1]; --j) {
+                std::swap(key[j], key[j - 1]);
+                std::swap(idx[j], idx[j - 1]);
+            }
+    };
+    sort_range(0, ns);
+    sort_range(ns, ns + ng);
+    for (uint32_t i = 0; i < ns; ++i) out[i] = p->wslist[idx[i]];
+    for (uint32_t i = 0; i < ng; ++i) {
+        out[ns + 2 * i] = p->wslist[ns + 2 * idx[ns + i]];
+        out[ns + 2 * i + 1] = p->wslist[ns + 2 * idx[ns + i] + 1];
+    }
+}
 
 constexpr int kScanThreads = 256;                        // threads per scan CTA
 constexpr int kScanWarps = kScanThreads / 32;

@@ -173,8 +173,10 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
                                          cudaMemcpyHostToDevice, st),
                          "upload masks");
         const uint64_t nl = pt->n_single + 2ull * pt->n_general;
+        uint4 list[64];  // at most 2 entries per position of the first 32
+        ordered_wslist(pt, text, list);
         if (!rc && nl)
-            rc = cuda_status(cudaMemcpyAsync(d_masks + where[q] + pt->nchunks, pt->wslist,
+            rc = cuda_status(cudaMemcpyAsync(d_masks + where[q] + pt->nchunks, list,
                                              nl * sizeof(uint4), cudaMemcpyHostToDevice, st),
                              "upload lists");
     }

@@ -39,9 +39,14 @@ __device__ __forceinline__ void code_word(uint32_t x, uint32_t &lo4, uint32_t &h
     hi4 = ((h * 0x00204081u) >> 21) & 0xfu;
 }
 
+// ctl[0]: first offset of a symbol outside ACGT (atomicMin); ctl[1..3]: how
+// many C, G, T the text holds (A: the rest; the padding of the last block
+// codes A, so it needs no correction).
 __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t first,
-                       uint2 *__restrict__ planes, unsigned long long *__restrict__ bad, int aligned)
+                       uint2 *__restrict__ planes, unsigned long long *__restrict__ ctl, int aligned)
 {
+    unsigned long long *bad = ctl;
+    uint32_t nc = 0, ng = 0, nt = 0;
     const uint64_t nb = (n + 31) / 32;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
@@ -85,6 +90,20 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t firs
             }
         }
         planes[first / 32 + b] = make_uint2(lo, hi);
+        nc += __popc(lo & ~hi);
+        ng += __popc(~lo & hi);
+        nt += __popc(lo & hi);
+    }
+    // letter counts: one atomic per warp and letter (at most 32 * 32 per
+    // thread-block row, far below 2^32 per warp over a grid-stride loop of
+    // n < 2^32 symbols)
+    nc = __reduce_add_sync(0xffffffffu, nc);
+    ng = __reduce_add_sync(0xffffffffu, ng);
+    nt = __reduce_add_sync(0xffffffffu, nt);
+    if ((threadIdx.x & 31) == 0) {
+        if (nc) atomicAdd(ctl + 1, (unsigned long long)nc);
+        if (ng) atomicAdd(ctl + 2, (unsigned long long)ng);
+        if (nt) atomicAdd(ctl + 3, (unsigned long long)nt);
     }
 }
 
@@ -175,14 +194,15 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
     pm_status rc = cuda_status(cudaMalloc(&t->planes, t->nblocks * sizeof(uint2)), "cudaMalloc planes");
     if (rc) { delete t; return rc; }
 
-    unsigned long long *bad = nullptr;
+    unsigned long long *bad = nullptr;  // [0] first bad offset, [1..3] C, G, T counts
     char *staging = nullptr;
     const bool on_device = is_device_pointer(ascii);
     const uint64_t body = (n + 31) / 32;
     rc = cuda_status(cudaMemsetAsync(t->planes + body, 0, (t->nblocks - body) * sizeof(uint2), st),
                      "memset padding");
-    if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, sizeof *bad, st), "cudaMallocAsync");
+    if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, 4 * sizeof *bad, st), "cudaMallocAsync");
     if (!rc) rc = cuda_status(cudaMemsetAsync(bad, 0xff, sizeof *bad, st), "memset");
+    if (!rc) rc = cuda_status(cudaMemsetAsync(bad + 1, 0, 3 * sizeof *bad, st), "memset");
     if (!rc && on_device) {
         rc = cuda_status(launch_pack(ascii, n, 0, t->planes, bad, st), "pack kernel");
     } else if (!rc && n > 0) {
@@ -196,9 +216,10 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
             if (!rc) rc = cuda_status(launch_pack(staging, len, off, t->planes, bad, st), "pack kernel");
         }
     }
-    unsigned long long h_bad = ~0ull;
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st),
+    unsigned long long h_ctl[4] = {~0ull, 0, 0, 0};
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(h_ctl, bad, sizeof h_ctl, cudaMemcpyDeviceToHost, st),
                               "copy status");
+    const unsigned long long h_bad = h_ctl[0];
     if (staging) cudaFreeAsync(staging, st);
     if (bad) cudaFreeAsync(bad, st);
     const cudaError_t se = cudaStreamSynchronize(st);
@@ -212,11 +233,25 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
         delete t;
         return rc;
     }
+    t->count[1] = h_ctl[1];
+    t->count[2] = h_ctl[2];
+    t->count[3] = h_ctl[3];
+    t->count[0] = n - h_ctl[1] - h_ctl[2] - h_ctl[3];
     *out = t;
     return PM_OK;
 }
 
 uint64_t pm_text_length(const pm_text *text) { return text ? text->n : 0; }
+
+pm_status pm_text_letter_counts(const pm_text *text, uint64_t counts[4])
+{
+    if (!text || !counts) {
+        set_error("pm_text_letter_counts: NULL argument");
+        return PM_E_ARG;
+    }
+    for (int i = 0; i < 4; ++i) counts[i] = text->count[i];
+    return PM_OK;
+}
 
 pm_status pm_text_device_planes(const pm_text *text, const void **planes, uint64_t *bytes)
 {

@@ -303,3 +303,29 @@ def test_auto_variant_table(pm):
         pm.pm_set_auto_variants([])
     assert pm.pm_get_auto_variants() == builtin
 
+
+
+def test_letter_counts_and_position_order(pm):
+    """pm_text_letter_counts equals a count of the ASCII text (host and device
+    input, ragged length, lower case); a text rich in one letter reorders the
+    window-sliced positions, which leaves every hit as the oracle has it."""
+    import torch
+    rng = np.random.default_rng(90)
+    for n in (1, 31, 4096 * 32 * 2 + 77):
+        text = synth.markov_text(n, seed=n)
+        want = [int(np.count_nonzero(text == ord(c))) for c in "ACGT"]
+        assert pm.pm_encode_text(text).letter_counts() == want
+        low = text.copy()
+        low[::3] |= 0x20
+        assert pm.pm_encode_text(torch.from_numpy(low).cuda()).letter_counts() == want
+    # 85 % T: positions asking for T are tested last, the rest first
+    n = 3 * 4096 * 32 + 5
+    text = np.frombuffer(np.where(rng.random(n) < 0.85, ord("T"),
+                                  rng.choice(np.frombuffer(b"ACG", np.uint8), n)).astype(np.uint8).tobytes(),
+                         np.uint8).copy()
+    pats = ["TTTTATTTTCTTTTGTTTTTRTTTYTTTTTTT" + "TTATT", "ACGTTTTTACGTTTTT", "TTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTT"]
+    for v in (0, 2):
+        for k in (0, 1, 2, 4):
+            got = gpu_hits(pm, text, pats, [k] * 3, variant=v)
+            for p, g in zip(pats, got):
+                same(g, oracle.search(text, p, k))
