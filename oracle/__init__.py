@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
             L.oracle_window_trace.argtypes = [vp, u64, c_p, u32, u64, i64, ctypes.c_int, vp, vp]
             L.oracle_counts.argtypes = [vp, u64, c_p, u32, vp, ctypes.POINTER(i64)]
             L.oracle_counts_at.argtypes = [vp, u64, c_p, u32, vp, u64, vp]
+            L.oracle_counts_unknown_text.argtypes = [vp, u64, c_p, u32, vp]
+            L.oracle_search_unknown_text.argtypes = [vp, u64, c_p, u32, i64, vp, vp, u64,
+                                                     ctypes.POINTER(u64)]
             L.oracle_search.argtypes = [vp, u64, c_p, u32, i64, ctypes.c_int, ctypes.c_int,
                                         vp, vp, vp, u64, ctypes.POINTER(u64),
                                         ctypes.POINTER(i64)]
@@ -200,3 +203,38 @@ def search(text, pattern, k: int, early_exit: bool = True, threads: int = 0,
             raise OracleError(f"oracle_search failed: {rc}")
         h = int(nh.value)
         return loc[:h].copy(), mm[:h].copy()
+
+
+def counts_unknown_text(text, pattern) -> np.ndarray:
+    """Full sums for every window of a text that may hold symbols outside
+    Table 1: such a symbol matches only the class N (see pm_oracle.c)."""
+    arr, n = _text_buf(text)
+    pb = _pat(pattern)
+    m = len(pb)
+    nwin = max(n - m + 1, 0)
+    out = np.zeros(max(nwin, 1), dtype=np.uint32)
+    rc = lib().oracle_counts_unknown_text(arr.ctypes.data, n, pb, m, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(f"oracle_counts_unknown_text failed: {rc}")
+    return out[:nwin]
+
+
+def search_unknown_text(text, pattern, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """search() for a text that may hold symbols outside Table 1 (one
+    thread): (locations uint32, mismatches uint32)."""
+    arr, n = _text_buf(text)
+    pb = _pat(pattern)
+    cap = 1 << 16
+    while True:
+        loc = np.empty(cap, dtype=np.uint32)
+        mm = np.empty(cap, dtype=np.uint32)
+        nh = ctypes.c_uint64(0)
+        rc = lib().oracle_search_unknown_text(arr.ctypes.data, n, pb, len(pb), int(k),
+                                              loc.ctypes.data, mm.ctypes.data, cap, ctypes.byref(nh))
+        if rc == E_OVERFLOW:
+            cap = int(nh.value)
+            continue
+        if rc != OK:
+            raise OracleError(f"oracle_search_unknown_text failed: {rc}")
+        return loc[:nh.value].copy(), mm[:nh.value].copy()
+

@@ -380,3 +380,80 @@ int oracle_search(const char *t, uint64_t n, const char *p, uint32_t m,
     free(r); free(pcs); free(th);
     return rc;
 }
+
+/* ---- Text symbols outside Table 1 --------------------------------------
+ * An extension the paper does not cover: its text alphabet has the four
+ * letters of Table 1, while genome files also carry N (and other letters)
+ * for bases that are not known.  Reading taken: such a text symbol is
+ * "unknown" (code 4 here); the pair test of an unknown text symbol with a
+ * pattern class is a match only for N, the class that holds every letter,
+ * and a mismatch for every other class and for "-".  Known symbols use
+ * Table 3 as before. */
+#define TEXT_UNKNOWN 4
+
+static uint8_t code_text_u(int ch)
+{
+    int c = oracle_text_code(ch);
+    return (uint8_t)(c < 0 ? TEXT_UNKNOWN : c);
+}
+
+/* r = p << 2 as in Sec. 2.3; N is code 14 of Table 2 */
+static uint32_t pair_u(uint8_t r, uint8_t tc)
+{
+    if (tc == TEXT_UNKNOWN) return (r >> 2) == 14 ? 0u : 1u;
+    return L[r | tc];
+}
+
+/* Full counts for windows 0..n-m of a text that may hold unknown symbols.
+ * out must hold n-m+1 entries.  For small inputs. */
+int oracle_counts_unknown_text(const char *t, uint64_t n, const char *p, uint32_t m,
+                               uint32_t *out)
+{
+    if (m == 0) return ORACLE_E_ARG;
+    uint8_t *tc = (uint8_t *)malloc(n ? n : 1);
+    uint8_t *r = (uint8_t *)malloc(m);
+    if (!tc || !r) { free(tc); free(r); return ORACLE_E_NOMEM; }
+    for (uint64_t i = 0; i < n; ++i) tc[i] = code_text_u((unsigned char)t[i]);
+    code_pattern_shifted(p, m, r);
+    if (m <= n)
+        for (uint64_t i = 0; i + m <= n; ++i) {
+            uint32_t s = 0;
+            for (uint32_t j = 0; j < m; ++j) s += pair_u(r[j], tc[i + j]);
+            out[i] = s;
+        }
+    free(tc); free(r);
+    return ORACLE_OK;
+}
+
+/* Eq. 4 with the early stop over a text that may hold unknown symbols: the
+ * 0-based locations whose sum is <= k, in order, with their sums (one
+ * thread).  Returns ORACLE_E_OVERFLOW with *nhits = the number needed when
+ * it exceeds cap. */
+int oracle_search_unknown_text(const char *t, uint64_t n, const char *p, uint32_t m, int64_t k,
+                               uint32_t *loc, uint32_t *mm, uint64_t cap, uint64_t *nhits)
+{
+    if (m == 0 || k < 0 || nhits == NULL) return ORACLE_E_ARG;
+    *nhits = 0;
+    if (m > n) return ORACLE_OK;
+    uint8_t *tc = (uint8_t *)malloc(n);
+    uint8_t *r = (uint8_t *)malloc(m);
+    if (!tc || !r) { free(tc); free(r); return ORACLE_E_NOMEM; }
+    for (uint64_t i = 0; i < n; ++i) tc[i] = code_text_u((unsigned char)t[i]);
+    code_pattern_shifted(p, m, r);
+    uint64_t h = 0;
+    for (uint64_t i = 0; i + m <= n; ++i) {
+        int64_t s = 0;
+        uint32_t j = 0;
+        for (; j < m; ++j) {
+            s += pair_u(r[j], tc[i + j]);
+            if (s > k) break;
+        }
+        if (s <= k) {
+            if (h < cap) { loc[h] = (uint32_t)i; mm[h] = (uint32_t)s; }
+            ++h;
+        }
+    }
+    free(tc); free(r);
+    *nhits = h;
+    return h > cap ? ORACLE_E_OVERFLOW : ORACLE_OK;
+}

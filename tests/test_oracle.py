@@ -281,3 +281,61 @@ def test_counts_at_matches_counts():
     full = oracle.counts(t, p)
     locs = np.array([0, 1, 17, 4989, 4990])
     assert oracle.counts_at(t, p, locs).tolist() == full[locs].tolist()
+
+
+# ---- text symbols outside Table 1 (an extension; the reading is that an
+# unknown text symbol matches the class N only) ----
+
+def test_unknown_text_oracle_equals_table1_oracle_without_unknowns():
+    rng = np.random.default_rng(500)
+    for case in range(20):
+        text = uniform_text(int(rng.integers(1, 400)), seed=500 + case)
+        m = int(rng.integers(1, 20))
+        pat = "".join(rng.choice(list("".join(IUPAC) + "-x"), size=m))
+        assert np.array_equal(oracle.counts_unknown_text(text, pat), oracle.counts(text, pat))
+        for k in (0, 2, 5):
+            got = oracle.search_unknown_text(text, pat, k)
+            want = oracle.search(text, pat, k, threads=1)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_unknown_text_is_the_worst_letter_at_each_unknown():
+    """With unknown symbols at a few offsets, every window's count equals the
+    largest count over all ways of writing letters there: an unknown symbol
+    mismatches every class but N, as the letter outside the class would."""
+    rng = np.random.default_rng(501)
+    for case in range(25):
+        n = int(rng.integers(8, 60))
+        text = uniform_text(n, seed=600 + case)
+        u = int(rng.integers(1, 4))
+        pos = rng.choice(n, size=u, replace=False)
+        t_unk = text.copy()
+        for q in pos:
+            t_unk[q] = ord(rng.choice(list("NnRx*")))
+        m = int(rng.integers(1, 9))
+        pat = "".join(rng.choice(list("".join(IUPAC) + "-"), size=m))
+        best = None
+        for letters in itertools.product(b"ACGT", repeat=u):
+            t = text.copy()
+            t[pos] = letters
+            c = oracle.counts(t, pat)
+            best = c if best is None else np.maximum(best, c)
+        assert np.array_equal(oracle.counts_unknown_text(t_unk, pat), best), (case, pat)
+
+
+def test_unknown_text_all_unknown_and_search_consistency():
+    text = np.frombuffer(b"N" * 50, dtype=np.uint8).copy()
+    for pat in ("ACGT", "NNNN", "ANNT-", "RYKMSWBDHVN"):
+        not_n = sum(1 for c in pat if c != "N")
+        c = oracle.counts_unknown_text(text, pat)
+        assert (c == not_n).all()
+    rng = np.random.default_rng(502)
+    text = uniform_text(3000, seed=502)
+    text[rng.choice(3000, size=300, replace=False)] = ord("N")
+    for m in (1, 7, 33):
+        pat = random_pattern(m, m // 3, rng)
+        full = oracle.counts_unknown_text(text, pat)
+        for k in (0, 3, 10):
+            loc, mm = oracle.search_unknown_text(text, pat, k)
+            want = np.nonzero(full <= k)[0]
+            assert np.array_equal(loc, want) and np.array_equal(mm, full[want])
