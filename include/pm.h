@@ -79,10 +79,30 @@ typedef struct pm_batch pm_batch;     /* patterns + k + scratch, resident on the
  */
 pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **out);
 
+/*
+ * pm_encode_text_ex -- pm_encode_text with flags.  flags = 0 is
+ * pm_encode_text.  PM_TEXT_UNKNOWN_AS_N accepts bytes outside Table 1 (for
+ * example N runs in genome files) instead of failing with PM_E_SYMBOL: each
+ * becomes an "unknown" symbol, which the pair test matches with the class N
+ * only (every other class, and "-", mismatch it).  The paper's text
+ * alphabet has the four letters only; this is an extension.  An unknown
+ * symbol costs one more bit of device memory per symbol (about 0.39 GB per
+ * 3.1 Gbp) for as long as the text holds one; searches of such a text
+ * recount the candidate windows exactly, so their results stay exact.
+ * Other flags: PM_E_ARG.
+ */
+#define PM_TEXT_UNKNOWN_AS_N 1u
+pm_status pm_encode_text_ex(const char *ascii, uint64_t n, uint32_t flags, void *stream,
+                            pm_text **out);
+
+/* Number of unknown symbols of an encoded text (0 unless it was coded with
+ * PM_TEXT_UNKNOWN_AS_N). */
+uint64_t pm_text_unknown(const pm_text *text);
+
 /* Number of symbols of an encoded text. */
 uint64_t pm_text_length(const pm_text *text);
-/* How many A, C, G, T (counts[0..3], Table 1 order) the text holds; they
- * sum to its length.  Counted while coding (pm_encode_text); the search uses
+/* How many A, C, G, T (counts[0..3], Table 1 order) the text holds; with
+ * pm_text_unknown they sum to its length.  Counted while coding (pm_encode_text); the search uses
  * them to order the positions it tests first (fewest matches first), which
  * changes no result.  PM_E_ARG for NULL arguments. */
 pm_status pm_text_letter_counts(const pm_text *text, uint64_t counts[4]);

@@ -11,9 +11,11 @@ is the Python binding, with the same names.
 """
 from ._native import (PM_E_ARG, PM_E_CUDA, PM_E_NOMEM, PM_E_OVERFLOW, PM_E_SYMBOL,  # noqa: F401
                       PM_E_TIMEOUT, PM_E_TOO_LARGE, PM_OK, PM_TOTAL_ERROR,
-                      PM_VARIANT_ALL_CHUNKS, PM_VARIANT_AUTO, PM_VARIANT_PATTERN_SLICED,
+                      PM_TEXT_UNKNOWN_AS_N, PM_VARIANT_ALL_CHUNKS, PM_VARIANT_AUTO,
+                      PM_VARIANT_PATTERN_SLICED,
                       PM_VARIANT_PATTERN_SLICED_2, PM_VARIANT_WINDOW_SLICED,
                       NativeLibraryMissing, PmError, lib)
 from .api import (Batch, GraphedBatch, Pattern, SearchResult, Text,  # noqa: F401
-                  pm_compile_pattern, pm_encode_text, pm_get_auto_variants, pm_search,
+                  pm_compile_pattern, pm_encode_text, pm_encode_text_ex, pm_get_auto_variants,
+                  pm_search,
                   pm_search_ex, pm_set_auto_variants)

@@ -24,6 +24,8 @@ PM_TOTAL_ERROR = (1 << 64) - 1
 PM_MAX_PATTERN = 1 << 24
 PM_MAX_BATCH = 1 << 16
 
+PM_TEXT_UNKNOWN_AS_N = 1
+
 PM_VARIANT_AUTO = 0
 PM_VARIANT_PATTERN_SLICED = 1
 PM_VARIANT_WINDOW_SLICED = 2
@@ -63,6 +65,8 @@ SIGNATURES = {
     "pm_text_length": (_u64, [_vp]),
     "pm_text_device_planes": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),
     "pm_text_free": (None, [_vp]),
+    "pm_encode_text_ex": (_i32, [_vp, _u64, _u32, _vp, ctypes.POINTER(_vp)]),
+    "pm_text_unknown": (_u64, [_vp]),
     "pm_text_letter_counts": (_i32, [_vp, ctypes.POINTER(_u64)]),
     "pm_compile_pattern": (_i32, [ctypes.c_char_p, _u32, ctypes.POINTER(_vp)]),
     "pm_pattern_length": (_u32, [_vp]),

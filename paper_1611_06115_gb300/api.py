@@ -56,6 +56,10 @@ class Text:
                 "pm_text_device_planes")
         return int(p.value or 0), int(b.value)
 
+    def unknown(self) -> int:
+        """Symbols coded as unknown (pm_text_unknown)."""
+        return int(N.lib().pm_text_unknown(self._h))
+
     def letter_counts(self) -> list[int]:
         """How many A, C, G, T the text holds (pm_text_letter_counts)."""
         arr = (ctypes.c_uint64 * 4)()
@@ -117,6 +121,17 @@ def pm_encode_text(ascii, stream=None) -> Text:
     out = ctypes.c_void_p()
     N.check(N.lib().pm_encode_text(ctypes.c_void_p(ptr), n, _stream(stream), ctypes.byref(out)),
             "pm_encode_text")
+    del keep
+    return Text(out, n)
+
+
+def pm_encode_text_ex(ascii, flags: int = 0, stream=None) -> Text:
+    """pm_encode_text with flags (include/pm.h); PM_TEXT_UNKNOWN_AS_N accepts
+    bytes outside ACGT as unknown symbols, matched by the class N only."""
+    ptr, n, keep = _buffer(ascii)
+    out = ctypes.c_void_p()
+    N.check(N.lib().pm_encode_text_ex(ctypes.c_void_p(ptr), n, int(flags), _stream(stream),
+                                      ctypes.byref(out)), "pm_encode_text_ex")
     del keep
     return Text(out, n)
 

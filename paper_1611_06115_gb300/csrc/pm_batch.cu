@@ -63,6 +63,7 @@ struct pm_batch {
     uint64_t runs;     // runs of `tiles` tiles covering them
     uint64_t capacity;
     const uint2 *planes;  // the text's planes (not owned)
+    const uint32_t *unk;  // the text's unknown-symbol bits or NULL (not owned)
     void *mem;            // one device allocation holding everything below
     pm::PatDesc *pats;
     uint32_t *order;      // pair indices, grouped
@@ -85,6 +86,7 @@ using namespace scan;
 
 struct BatchArgs {
     const uint2 *planes;
+    const uint32_t *unk;
     const PatDesc *pats;
     const uint32_t *order;
     const uint32_t *gkind;
@@ -111,6 +113,7 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
                                            const uint4 *__restrict__ M, const BatchArgs &ba)
 {
     const int lane = threadIdx.x & 31;
+    if (ba.unk) pass = recount_unknown(pass, ba.planes, ba.unk, blk, M, nchunks, k);
     const uint32_t nh = __popc(pass);
     uint32_t incl = nh;
 #pragma unroll
@@ -119,6 +122,7 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
         if (lane >= o) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;  // every candidate dropped by the recount (warp-uniform)
     unsigned long long base = 0;
     if (lane == 0) {
         base = atomicAdd(ba.cursor, (unsigned long long)total);
@@ -133,7 +137,7 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
         const uint32_t w = __ffs(hm) - 1;
         hm &= hm - 1;
         if (q < ba.cap) {
-            const uint32_t c = window_count_from(ba.planes, blk, w, M, 0, nchunks, 0u, k);
+            const uint32_t c = window_count_exact(ba.planes, ba.unk, blk, w, M, nchunks, k);
             ba.tmp[q] = pm_hit{(uint32_t)(blk * 32ull + w), c};
         }
         ++q;
@@ -546,6 +550,7 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
     b->nphases = (uint32_t)phases.size();
     b->capacity = capacity;
     b->planes = text->planes;
+    b->unk = text->unk;
     const unsigned long long max_key = (unsigned long long)npat * (b->ntiles ? b->ntiles : 1) * G;
     b->key_bits = 0;
     while (b->key_bits < 64 && (max_key >> b->key_bits) != 0) ++b->key_bits;
@@ -630,7 +635,7 @@ pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *strea
     if (rc) return rc;
     const uint64_t items = b->runs * b->nphases;
     if (items > 0) {
-        BatchArgs ba{b->planes, b->pats,  b->order,  b->gkind, b->phases,  b->arena,
+        BatchArgs ba{b->planes, b->unk, b->pats,  b->order,  b->gkind, b->phases,  b->arena,
                      b->npat,   b->ngroups, b->tiles, b->ntiles, b->runs, items,
                      b->tmp,    b->capacity, cursor,  b->recs,  b->capacity, rec_cursor,
                      b->pat_counts, status};

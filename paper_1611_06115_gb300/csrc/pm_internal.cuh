@@ -22,11 +22,14 @@
 #include "pm.h"
 
 struct pm_text {
-    uint64_t n;         // symbols
-    uint64_t nblocks;   // allocated blocks, padding included
-    uint2 *planes;      // device
+    uint64_t n;          // symbols
+    uint64_t nblocks;    // allocated blocks, padding included
+    uint2 *planes;       // device
+    uint32_t *unk;       // device, one bit per symbol outside Table 1 (block layout of the
+                         //   planes, zero padded); NULL when the text has none
     int device;
-    uint64_t count[4];  // how many A, C, G, T the text holds (Table 1 order)
+    uint64_t count[4];   // how many A, C, G, T the text holds (Table 1 order)
+    uint64_t n_unknown;  // symbols outside Table 1 (coded as some letter in the planes)
 };
 
 struct pm_pattern {
@@ -140,9 +143,9 @@ enum class Variant : int {
 Variant resolve_variant(Variant v, int32_t k);
 
 // Launch one scan kernel for one pattern (pm_scan.cu).
-cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *arena,
-                        TileEntry *table, pm_hit *tmp, uint64_t cap, unsigned long long *cursor,
-                        uint32_t *status, int grid, cudaStream_t stream);
+cudaError_t launch_scan(Variant v, const uint2 *planes, const uint32_t *unk, const PatDesc &d,
+                        const uint4 *arena, TileEntry *table, pm_hit *tmp, uint64_t cap,
+                        unsigned long long *cursor, uint32_t *status, int grid, cudaStream_t stream);
 
 // Number of resident scan CTAs the device runs at once (pm_scan.cu).
 int scan_grid_limit(Variant v, int32_t k, int device);
@@ -225,7 +228,7 @@ cudaError_t launch_order_records(const TileEntry *entries, uint64_t n_max,
 
 // Text coding kernel (pm_text.cu).
 cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol,
-                        uint2 *planes, unsigned long long *bad, cudaStream_t stream);
+                        uint2 *planes, uint32_t *unk, unsigned long long *bad, cudaStream_t stream);
 
 // Thread-local detailed error message.
 void set_error(const char *fmt, ...);

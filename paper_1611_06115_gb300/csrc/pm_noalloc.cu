@@ -189,7 +189,7 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
     if (!rc) rc = cuda_status(cudaMemsetAsync(ctl, 0, 256, st), "clear control words");
     for (uint32_t p = 0; !rc && p < npat; ++p) {
         const Variant v = auto_variant(desc[p], dev);
-        rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
+        rc = cuda_status(launch_scan(v, text->planes, text->unk, desc[p], d_masks, d_table, d_tmp, capacity,
                                      d_cursor, d_status, scan_grid_limit(v, desc[p].k, dev), st),
                          "scan kernel");
     }

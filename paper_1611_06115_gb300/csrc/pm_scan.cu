@@ -52,7 +52,8 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
-           unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status)
+           unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status,
+           const uint32_t *__restrict__ unk)
 {
     constexpr bool kWS = VARIANT >= 0;
 
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
         if (__any_sync(kFull, anyp != 0u)) {
             uint32_t total;
             unsigned long long base;
-            emit_tile_hits(pass, blk, d, M, planes, tmp, cap, cursor, total, base);
+            emit_tile_hits(pass, blk, d, M, planes, unk, tmp, cap, cursor, total, base);
             if (lane == 0) table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
         } else if (lane == 0) {
             table[d.tile0 + tile] = TileEntry{0u, 0u};
@@ -260,9 +261,9 @@ int scan_grid_limit(Variant v, int32_t k, int device)
     return cache[device][slot];
 }
 
-cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const uint4 *arena,
-                        TileEntry *table, pm_hit *tmp, uint64_t cap, unsigned long long *cursor,
-                        uint32_t *status, int grid, cudaStream_t stream)
+cudaError_t launch_scan(Variant v, const uint2 *planes, const uint32_t *unk, const PatDesc &d,
+                        const uint4 *arena, TileEntry *table, pm_hit *tmp, uint64_t cap,
+                        unsigned long long *cursor, uint32_t *status, int grid, cudaStream_t stream)
 {
     if (d.ntiles == 0) return cudaSuccess;
     const uint64_t ctas_needed = (d.ntiles + kScanWarps - 1) / kScanWarps;
@@ -270,8 +271,8 @@ cudaError_t launch_scan(Variant v, const uint2 *planes, const PatDesc &d, const 
     if (grid < 1) grid = 1;
     const void *fn = select_kernel(resolve_variant(v, d.k), d.k);
     PatDesc dd = d;
-    void *args[] = {(void *)&planes, (void *)&dd, (void *)&arena, (void *)&table,
-                    (void *)&tmp,    (void *)&cap, (void *)&cursor, (void *)&status};
+    void *args[] = {(void *)&planes, (void *)&dd,     (void *)&arena,  (void *)&table, (void *)&tmp,
+                    (void *)&cap,    (void *)&cursor, (void *)&status, (void *)&unk};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kScanThreads), args, 0, stream);
 }
 

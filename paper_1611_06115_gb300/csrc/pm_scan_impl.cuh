@@ -32,6 +32,53 @@ __device__ __forceinline__ uint32_t window_count_from(const uint2 *__restrict__ 
     return count;
 }
 
+// The exact count of window 32*blk + w (stopping once past `limit`) for a
+// text that may hold unknown symbols (unk: one bit per symbol, NULL when the
+// text has none).  At an unknown symbol only the class N (every letter)
+// matches.  The planes code an unknown symbol as some letter, so the count
+// the scan evaluations see there is never above this one: a window they
+// drop is past k here too, and the windows they pass are recounted here.
+__device__ __forceinline__ uint32_t window_count_exact(const uint2 *__restrict__ planes,
+                                                       const uint32_t *__restrict__ unk,
+                                                       uint64_t blk, uint32_t w,
+                                                       const uint4 *__restrict__ M,
+                                                       uint32_t nchunks, uint32_t limit)
+{
+    if (!unk) return window_count_from(planes, blk, w, M, 0, nchunks, 0u, limit);
+    uint32_t count = 0;
+    uint2 a = __ldg(planes + blk);
+    uint32_t ua = __ldg(unk + blk);
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        const uint2 b = __ldg(planes + blk + c + 1);
+        const uint32_t ub = __ldg(unk + blk + c + 1);
+        const uint4 Mc = __ldg(M + c);
+        const uint32_t match = class_match(__funnelshift_r(a.x, b.x, w), __funnelshift_r(a.y, b.y, w), Mc);
+        const uint32_t u = __funnelshift_r(ua, ub, w);
+        const uint32_t is_n = Mc.x & Mc.y & Mc.z & Mc.w;  // also every position past m
+        count += __popc(~((match & ~u) | (u & is_n)));
+        if (count > limit) break;
+        a = b;
+        ua = ub;
+    }
+    return count;
+}
+
+// Drop from pass the windows whose exact count (window_count_exact) is past
+// k; only texts with unknown symbols need it.
+__device__ __forceinline__ uint32_t recount_unknown(uint32_t pass, const uint2 *__restrict__ planes,
+                                                   const uint32_t *__restrict__ unk, uint64_t blk,
+                                                   const uint4 *__restrict__ M, uint32_t nchunks,
+                                                   uint32_t k)
+{
+    uint32_t sv = pass;
+    while (sv) {
+        const uint32_t w = __ffs(sv) - 1;
+        sv &= sv - 1;
+        if (window_count_exact(planes, unk, blk, w, M, nchunks, k) > k) pass &= ~(1u << w);
+    }
+    return pass;
+}
+
 __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
 {
     uint32_t r;
@@ -342,14 +389,20 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
 // warp-aggregated atomic on cursor.  Call with the whole warp and only when
 // some lane has a pass bit.  Returns (on every lane) the number of hits and
 // where they start in tmp.
-__device__ __forceinline__ void emit_tile_hits(const uint32_t (&pass)[G], const uint64_t (&blk)[G],
+__device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64_t (&blk)[G],
                                                const PatDesc &d, const uint4 *__restrict__ M,
                                                const uint2 *__restrict__ planes,
+                                               const uint32_t *__restrict__ unk,
                                                pm_hit *__restrict__ tmp, uint64_t cap,
                                                unsigned long long *__restrict__ cursor,
                                                uint32_t &total_out, unsigned long long &base_out)
 {
     const int lane = threadIdx.x & 31;
+    if (unk) {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            pass[g] = recount_unknown(pass[g], planes, unk, blk[g], M, d.nchunks, (uint32_t)d.k);
+    }
     uint32_t incl[G], tot[G];
     uint32_t total = 0;
 #pragma unroll
@@ -376,8 +429,8 @@ __device__ __forceinline__ void emit_tile_hits(const uint32_t (&pass)[G], const 
             const uint32_t w = __ffs(hm) - 1;
             hm &= hm - 1;
             if (q < cap) {
-                const uint32_t c = window_count_from(planes, blk[g], w, M, 0, d.nchunks, 0u,
-                                                     (uint32_t)d.k);
+                const uint32_t c = window_count_exact(planes, unk, blk[g], w, M, d.nchunks,
+                                                      (uint32_t)d.k);
                 tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
             }
             ++q;

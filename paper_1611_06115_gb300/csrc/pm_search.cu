@@ -206,7 +206,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                               : resolve_variant(variant_from_public(o.variant), desc[p].k);
         const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, desc[p].k, dev);
         if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p], st);
-        rc = cuda_status(launch_scan(v, text->planes, desc[p], d_masks, d_table, d_tmp, capacity,
+        rc = cuda_status(launch_scan(v, text->planes, text->unk, desc[p], d_masks, d_table, d_tmp, capacity,
                                      d_cursor, d_status, grid, st),
                          "scan kernel");
         if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p + 1], st);

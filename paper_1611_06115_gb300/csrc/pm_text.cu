@@ -39,14 +39,17 @@ __device__ __forceinline__ void code_word(uint32_t x, uint32_t &lo4, uint32_t &h
     hi4 = ((h * 0x00204081u) >> 21) & 0xfu;
 }
 
-// ctl[0]: first offset of a symbol outside ACGT (atomicMin); ctl[1..3]: how
-// many C, G, T the text holds (A: the rest; the padding of the last block
-// codes A, so it needs no correction).
+// ctl[0]: first offset of a symbol outside ACGT (atomicMin), unless unk is
+// given: then such symbols are recorded there (one bit per symbol, the
+// planes' block layout) and counted in ctl[4].  ctl[1..3]: how many C, G, T
+// the text holds (A: the rest; the padding of the last block codes A, so it
+// needs no correction).
 __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t first,
-                       uint2 *__restrict__ planes, unsigned long long *__restrict__ ctl, int aligned)
+                       uint2 *__restrict__ planes, uint32_t *__restrict__ unk,
+                       unsigned long long *__restrict__ ctl, int aligned)
 {
     unsigned long long *bad = ctl;
-    uint32_t nc = 0, ng = 0, nt = 0;
+    uint32_t nc = 0, ng = 0, nt = 0, nu = 0;
     const uint64_t nb = (n + 31) / 32;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
@@ -70,7 +73,7 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t firs
                 w[q] = v;
             }
         }
-        uint32_t lo = 0, hi = 0;
+        uint32_t lo = 0, hi = 0, ub = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             uint32_t l4, h4;
@@ -83,16 +86,22 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t firs
                     const uint32_t ch = (w[q] >> (8 * i)) & 0xffu;
                     const uint32_t u = ch & 0xdfu;
                     if (u != 'A' && u != 'C' && u != 'G' && u != 'T') {
-                        atomicMin(bad, (unsigned long long)(first + off + 4 * q + i));
-                        break;
+                        if (unk) {
+                            ub |= 1u << (4 * q + i);
+                        } else {
+                            atomicMin(bad, (unsigned long long)(first + off + 4 * q + i));
+                            break;
+                        }
                     }
                 }
             }
         }
         planes[first / 32 + b] = make_uint2(lo, hi);
-        nc += __popc(lo & ~hi);
-        ng += __popc(~lo & hi);
-        nt += __popc(lo & hi);
+        if (unk) unk[first / 32 + b] = ub;
+        nc += __popc(lo & ~hi & ~ub);
+        ng += __popc(~lo & hi & ~ub);
+        nt += __popc(lo & hi & ~ub);
+        nu += __popc(ub);
     }
     // letter counts: one atomic per warp and letter (at most 32 * 32 per
     // thread-block row, far below 2^32 per warp over a grid-stride loop of
@@ -100,10 +109,12 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t firs
     nc = __reduce_add_sync(0xffffffffu, nc);
     ng = __reduce_add_sync(0xffffffffu, ng);
     nt = __reduce_add_sync(0xffffffffu, nt);
+    nu = __reduce_add_sync(0xffffffffu, nu);
     if ((threadIdx.x & 31) == 0) {
         if (nc) atomicAdd(ctl + 1, (unsigned long long)nc);
         if (ng) atomicAdd(ctl + 2, (unsigned long long)ng);
         if (nt) atomicAdd(ctl + 3, (unsigned long long)nt);
+        if (nu) atomicAdd(ctl + 4, (unsigned long long)nu);
     }
 }
 
@@ -136,7 +147,7 @@ bool is_device_pointer(const void *p)
 }
 
 cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol, uint2 *planes,
-                        unsigned long long *bad, cudaStream_t stream)
+                        uint32_t *unk, unsigned long long *bad, cudaStream_t stream)
 {
     if (n_chunk == 0) return cudaSuccess;
     const uint64_t nb = (n_chunk + 31) / 32;
@@ -147,7 +158,7 @@ cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symb
     const uint64_t cap = (uint64_t)sms * 16;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     const int aligned = ((uintptr_t)ascii % 16) == 0;
-    k_pack<<<grid, 256, 0, stream>>>(ascii, n_chunk, first_symbol, planes, bad, aligned);
+    k_pack<<<grid, 256, 0, stream>>>(ascii, n_chunk, first_symbol, planes, unk, bad, aligned);
     return cudaGetLastError();
 }
 
@@ -176,10 +187,16 @@ const char *pm_status_string(pm_status s)
 
 pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **out)
 {
-    if (!out || (!ascii && n > 0)) {
-        set_error("pm_encode_text: NULL argument");
+    return pm_encode_text_ex(ascii, n, 0u, stream, out);
+}
+
+pm_status pm_encode_text_ex(const char *ascii, uint64_t n, uint32_t flags, void *stream, pm_text **out)
+{
+    if (!out || (!ascii && n > 0) || (flags & ~PM_TEXT_UNKNOWN_AS_N)) {
+        set_error("pm_encode_text: NULL argument or unknown flags 0x%x", flags);
         return PM_E_ARG;
     }
+    const bool allow_unknown = (flags & PM_TEXT_UNKNOWN_AS_N) != 0;
     *out = nullptr;
     if (n >= (1ull << 32)) {
         set_error("pm_encode_text: n = %llu >= 2^32", (unsigned long long)n);
@@ -193,18 +210,25 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
     t->nblocks = (n + 31) / 32 + kPadBlocks;
     pm_status rc = cuda_status(cudaMalloc(&t->planes, t->nblocks * sizeof(uint2)), "cudaMalloc planes");
     if (rc) { delete t; return rc; }
+    if (allow_unknown) {
+        rc = cuda_status(cudaMalloc(&t->unk, t->nblocks * sizeof(uint32_t)), "cudaMalloc unknown bits");
+        if (rc) { cudaFree(t->planes); delete t; return rc; }
+    }
 
-    unsigned long long *bad = nullptr;  // [0] first bad offset, [1..3] C, G, T counts
+    unsigned long long *bad = nullptr;  // [0] first bad offset, [1..3] C, G, T, [4] unknown counts
     char *staging = nullptr;
     const bool on_device = is_device_pointer(ascii);
     const uint64_t body = (n + 31) / 32;
     rc = cuda_status(cudaMemsetAsync(t->planes + body, 0, (t->nblocks - body) * sizeof(uint2), st),
                      "memset padding");
-    if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, 4 * sizeof *bad, st), "cudaMallocAsync");
+    if (!rc && t->unk)
+        rc = cuda_status(cudaMemsetAsync(t->unk + body, 0, (t->nblocks - body) * sizeof(uint32_t), st),
+                         "memset padding");
+    if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, 5 * sizeof *bad, st), "cudaMallocAsync");
     if (!rc) rc = cuda_status(cudaMemsetAsync(bad, 0xff, sizeof *bad, st), "memset");
-    if (!rc) rc = cuda_status(cudaMemsetAsync(bad + 1, 0, 3 * sizeof *bad, st), "memset");
+    if (!rc) rc = cuda_status(cudaMemsetAsync(bad + 1, 0, 4 * sizeof *bad, st), "memset");
     if (!rc && on_device) {
-        rc = cuda_status(launch_pack(ascii, n, 0, t->planes, bad, st), "pack kernel");
+        rc = cuda_status(launch_pack(ascii, n, 0, t->planes, t->unk, bad, st), "pack kernel");
     } else if (!rc && n > 0) {
         const uint64_t chunk = n < kHostChunk ? n : kHostChunk;
         rc = cuda_status(cudaMallocAsync((void **)&staging, (chunk + 15) & ~15ull, st),
@@ -213,10 +237,10 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
             const uint64_t len = n - off < kHostChunk ? n - off : kHostChunk;
             rc = cuda_status(cudaMemcpyAsync(staging, ascii + off, len, cudaMemcpyHostToDevice, st),
                              "copy text to device");
-            if (!rc) rc = cuda_status(launch_pack(staging, len, off, t->planes, bad, st), "pack kernel");
+            if (!rc) rc = cuda_status(launch_pack(staging, len, off, t->planes, t->unk, bad, st), "pack kernel");
         }
     }
-    unsigned long long h_ctl[4] = {~0ull, 0, 0, 0};
+    unsigned long long h_ctl[5] = {~0ull, 0, 0, 0, 0};
     if (!rc) rc = cuda_status(cudaMemcpyAsync(h_ctl, bad, sizeof h_ctl, cudaMemcpyDeviceToHost, st),
                               "copy status");
     const unsigned long long h_bad = h_ctl[0];
@@ -230,18 +254,26 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
     }
     if (rc) {
         cudaFree(t->planes);
+        if (t->unk) cudaFree(t->unk);
         delete t;
         return rc;
+    }
+    t->n_unknown = h_ctl[4];
+    if (t->unk && t->n_unknown == 0) {  // nothing unknown: the searches skip the recount
+        cudaFree(t->unk);
+        t->unk = nullptr;
     }
     t->count[1] = h_ctl[1];
     t->count[2] = h_ctl[2];
     t->count[3] = h_ctl[3];
-    t->count[0] = n - h_ctl[1] - h_ctl[2] - h_ctl[3];
+    t->count[0] = n - h_ctl[1] - h_ctl[2] - h_ctl[3] - h_ctl[4];
     *out = t;
     return PM_OK;
 }
 
 uint64_t pm_text_length(const pm_text *text) { return text ? text->n : 0; }
+
+uint64_t pm_text_unknown(const pm_text *text) { return text ? text->n_unknown : 0; }
 
 pm_status pm_text_letter_counts(const pm_text *text, uint64_t counts[4])
 {
@@ -268,6 +300,7 @@ void pm_text_free(pm_text *text)
     cudaGetDevice(&cur);
     if (cur != text->device) cudaSetDevice(text->device);
     cudaFree(text->planes);
+    if (text->unk) cudaFree(text->unk);
     if (cur != text->device) cudaSetDevice(cur);
     delete text;
 }
