@@ -587,10 +587,10 @@ def run_serving(a):
 
 
 def run_profile(a):
-    """Four single searches of the GENOME m = 128 pattern over the first n
+    """Five single searches of the GENOME m = 128 pattern over the first n
     symbols, one per kernel kind, for a small ncu capture:
     (pattern-sliced, k = 4), (window-sliced, 0), (window-sliced, 4),
-    (pattern-sliced, 16)."""
+    (pattern-sliced, 16), (pattern-sliced over 64 positions, 24)."""
     import torch
     import paper_1611_06115_gb300 as pm
     pats = genome_patterns()
@@ -598,7 +598,7 @@ def run_profile(a):
     build_text(a.n, 0, host.numpy(), pats)
     text = pm.pm_encode_text(host)
     c = pm.pm_compile_pattern(pats[1])
-    for v, k in ((1, 4), (2, 0), (2, 4), (1, 16)):
+    for v, k in ((1, 4), (2, 0), (2, 4), (1, 16), (3, 24)):
         r = pm.pm_search_ex(text, [c], [k], variant=v)
         print(json.dumps({"variant": v, "k": k, "hits": r.total}), flush=True)
 
