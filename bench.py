@@ -47,6 +47,21 @@ TEXT_SEED = 3
 METRIC = "window-cells/s"
 VARIANT_NAMES = {1: "pattern-sliced", 2: "window-sliced", 3: "pattern-sliced-64", 4: "all-chunks"}
 
+# DRAM bytes (read + write) of one pattern-sliced (k = 16, m = 128) launch over
+# the GENOME text at n = 8e8, from the ncu capture summarised in
+# profiles/k_scan_ncu_full_800M.md; scaled by the window count of a launch.
+# Valid for that kernel as captured: set it to None when the kernel changes.
+TRAFFIC_KERNEL = "k_scan<pattern-sliced>"
+TRAFFIC_BYTES_8E8 = (200.058880 + 4.104192) * 1e6
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, k = 16 m = 128 launch at "
+                  "n = 8e8 (profiles/k_scan_ncu_full_800M.md), scaled by windows")
+
+
+def traffic(kernel, n):
+    if TRAFFIC_BYTES_8E8 is None or kernel != TRAFFIC_KERNEL:
+        return None
+    return TRAFFIC_BYTES_8E8 * (n - 127) / (800_000_000 - 127)
+
 
 def args_():
     ap = argparse.ArgumentParser()
@@ -398,7 +413,8 @@ def run_ours(a):
         "gpu_launches": a.steps * (len(ents) + 5),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic(dom, n_local),
+                     "traffic_source": TRAFFIC_SOURCE if traffic(dom, n_local) else None,
                      "kernel": dom, "kernel_ms": dom_ms,
                      "launches": [f"m={len(ents[e][0])},k={ents[e][1]}" for e in dom_e],
                      "alu": alu,
