@@ -80,6 +80,8 @@ def args_():
                          "lines; profile runs four single searches for an ncu capture")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: queries per second")
+    ap.add_argument("--serve-mode", choices=("one-launch", "launch-per-query"), default="launch-per-query",
+                    help="serving: one persistent launch per batch, or one scan launch per query")
     return ap.parse_args()
 
 
@@ -582,7 +584,7 @@ def run_serving(a):
     text = pm.pm_encode_text(host)
     qs = workloads.serving_queries(rate=a.rate, duration=a.duration)
     queries = [(q.arrival, q.pattern, q.k) for q in qs]
-    backend = serve.GpuBackend(text, slots=4)
+    backend = serve.GpuBackend(text, slots=4, batch={} if a.serve_mode == "one-launch" else None)
     # warm the kernels and the pool
     srv = serve.Server(backend, n=n, slots=4, max_batch=32, mem_budget=32 << 30)
     serve.run_trace(srv, queries[:20])
@@ -593,7 +595,7 @@ def run_serving(a):
     torch.cuda.synchronize()
     ck = clocks.stop()
     n_cells = sum((n - len(r.pattern) + 1) * len(r.pattern) for r in srv.done)
-    stats.update({"workload": "SERVING", "n": n, "offered_rate_qps": a.rate,
+    stats.update({"workload": "SERVING", "mode": a.serve_mode, "n": n, "offered_rate_qps": a.rate,
                   "arrival_seconds": a.duration, "queries": len(queries),
                   "window_cells_per_s": n_cells / stats["span_s"],
                   "hits": int(sum(max(r.count, 0) for r in srv.done)), "clocks": ck,

@@ -209,16 +209,26 @@ pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint
  * events    NULL, or 2*npat cudaEvent_t handles (created by the caller on
  *           the current device); events[2p] and events[2p+1] are recorded on
  *           the stream just before and just after pattern p's scan kernel.
+ * batch     NULL: one scan launch per pattern (variant and grid as above).
+ *           Otherwise all pairs run in ONE persistent launch as in
+ *           pm_batch_create / pm_batch_run with these batch options, the
+ *           scratch (about 56 bytes per unit of capacity) taken from the
+ *           stream-ordered pool and released on the stream: nothing waits
+ *           unless `needed` or host outputs ask for it.  variant, grid and
+ *           events are then ignored, except that events must be NULL
+ *           (PM_E_ARG).
  */
 #define PM_VARIANT_AUTO 0
 #define PM_VARIANT_PATTERN_SLICED 1
 #define PM_VARIANT_WINDOW_SLICED 2
 #define PM_VARIANT_PATTERN_SLICED_2 3
 #define PM_VARIANT_ALL_CHUNKS 4
+struct pm_batch_options;
 typedef struct pm_options {
     int32_t variant;
     int32_t grid;
     void *const *events;
+    const struct pm_batch_options *batch;
 } pm_options;
 
 pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
@@ -267,8 +277,7 @@ pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
  *                  outlive the batch.  Waits for its uploads.
  * options          NULL for defaults, or (0 in any field: its default):
  *                    group      pairs per work item, rounded up to a
- *                               multiple of 8 (default: all pairs of one
- *                               kind of evaluation);
+ *                               multiple of 8 (default 16);
  *                    grid       CTAs of the persistent launch (default: as
  *                               many as the device keeps resident);
  *                    tiles      warp tiles of 4096 windows per work item,

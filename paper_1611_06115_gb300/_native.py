@@ -47,15 +47,16 @@ class pm_hit(ctypes.Structure):
     _fields_ = [("location", ctypes.c_uint32), ("mismatches", ctypes.c_uint32)]
 
 
-class pm_options(ctypes.Structure):
-    _fields_ = [("variant", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("events", ctypes.POINTER(ctypes.c_void_p))]
-
-
 class pm_batch_options(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("grid", ctypes.c_int32), ("tiles", ctypes.c_int32),
                 ("ws_below", ctypes.c_int32), ("ps1_below", ctypes.c_int32),
                 ("ps2_below", ctypes.c_int32)]
+
+
+class pm_options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("events", ctypes.POINTER(ctypes.c_void_p)),
+                ("batch", ctypes.POINTER(pm_batch_options))]
 
 
 # Every function include/pm.h declares, with (restype, argtypes).

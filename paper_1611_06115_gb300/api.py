@@ -179,7 +179,7 @@ def _event_handles(events) -> ctypes.Array | None:
 
 def pm_search_ex(text: Text, patterns, k, capacity: int | None = None, out: str = "device",
                  stream=None, variant: int = N.PM_VARIANT_AUTO, grid: int = 0, events=None,
-                 sync: bool = True) -> SearchResult:
+                 sync: bool = True, batch: dict | None = None) -> SearchResult:
     """Search every pattern (with its k) over the text; see pm_search in include/pm.h.
 
     capacity None: start from an estimate and grow on PM_E_OVERFLOW.
@@ -188,6 +188,9 @@ def pm_search_ex(text: Text, patterns, k, capacity: int | None = None, out: str 
     ``result.offsets[-1]`` after the stream to learn the total.
     events: None or 2 * len(patterns) torch.cuda.Event objects, already created
     (recorded once), recorded around each pattern's scan kernel.
+    batch: None for one scan launch per pattern, else a dict of batch options
+    (``Batch.OPTIONS``; {} for the defaults): all pairs in one persistent
+    launch with stream-ordered scratch.
     """
     pats = list(patterns)
     npat = len(pats)
@@ -199,7 +202,14 @@ def pm_search_ex(text: Text, patterns, k, capacity: int | None = None, out: str 
     ev = _event_handles(events)
     if ev is not None and len(ev) != 2 * npat:
         raise ValueError("events must hold 2 per pattern")
-    opts = N.pm_options(variant, grid, ctypes.cast(ev, ctypes.POINTER(ctypes.c_void_p)) if ev else None)
+    bopts = None
+    if batch is not None:
+        unknown = set(batch) - set(Batch.OPTIONS)
+        if unknown:
+            raise ValueError(f"unknown batch options {sorted(unknown)}")
+        bopts = N.pm_batch_options(**{name: int(batch.get(name, 0)) for name in Batch.OPTIONS})
+    opts = N.pm_options(variant, grid, ctypes.cast(ev, ctypes.POINTER(ctypes.c_void_p)) if ev else None,
+                        ctypes.pointer(bopts) if bopts is not None else None)
     grow = capacity is None
     cap = int(capacity) if capacity is not None else 1 << 20
     if not sync and (out != "device" or grow):

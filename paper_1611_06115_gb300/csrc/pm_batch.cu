@@ -152,7 +152,9 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
 // exactly when matches + k >= 32C, i.e. when the window has at most k
 // mismatches in those positions.  Windows that pass and whose pattern is
 // longer are then counted exactly (settle_staged).
-template <int C>
+// kAll: all kP slots hold pairs (every group but the last of a category);
+// otherwise the empty slots are skipped.
+template <int C, bool kAll>
 __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t pfirst,
                                             uint32_t cnt, uint4 *sM0, uint4 *sM1, uint4 *sP,
                                             const BatchArgs &ba)
@@ -161,7 +163,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
     const uint32_t two = ba.pats[ba.order[pfirst]].two;
     const uint32_t m1 = C == 1 ? two << 1 : two, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
     if (lane < kP) {
-        // slots past cnt repeat a real pair: evaluated, never emitted
+        // slots past cnt repeat a real pair (never evaluated)
         const uint32_t pi = __ldg(ba.order + pfirst + lane);
         const PatDesc &dl = ba.pats[pi];
         const uint32_t kl = (uint32_t)dl.k;
@@ -194,6 +196,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
             }
 #pragma unroll
             for (int p = 0; p < kP; ++p) {
+                if (!kAll && p >= (int)cnt) break;  // warp-uniform
                 const uint4 M0 = sM0[p];
                 uint32_t gm[4];
 #pragma unroll
@@ -257,38 +260,53 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
     }
     __syncwarp();
 
-    const uint64_t stride = (uint64_t)gridDim.x * kScanWarps;
+    // runs < 2^21 (a text has fewer than 2^32 symbols) and the grid is
+    // resident, so 32-bit positions suffice
+    const uint32_t stride = gridDim.x * kScanWarps;
     const uint32_t T = ba.tiles;
-    // sequence positions as (item, tile within its run of T)
-    auto advance = [&](uint64_t &i, uint32_t &u) {
-        if (++u == T) {
-            u = 0;
-            i += stride;
+    const uint32_t runs = (uint32_t)ba.runs;
+    const uint32_t nrows = (uint32_t)(ba.items / ba.runs);
+    // Sequence positions as (row, run, tile within the run of T): work item
+    // row * runs + run.  Moving on by `stride` items needs no division (this
+    // runs once per tile; a 64-bit division would cost more than a cheap
+    // tile's evaluation).
+    struct Pos {
+        uint32_t row, u, run;
+    };
+    auto advance = [&](Pos &q) {
+        if (++q.u == T) {
+            q.u = 0;
+            q.run += stride;
+            while (q.run >= runs && q.row < nrows) {
+                q.run -= runs;
+                ++q.row;
+            }
         }
     };
-    auto tile_of = [&](uint64_t i, uint32_t u) { return (i % ba.runs) * T + u; };
-    uint64_t ci = (uint64_t)blockIdx.x * kScanWarps + warp, pi = ci;  // consumed, next to stage
-    uint32_t cu = 0, pu = 0;
+    auto tile_of = [&](const Pos &q) { return (uint64_t)q.run * T + q.u; };
+    const uint32_t first = blockIdx.x * kScanWarps + warp;
+    Pos cp{first / runs, 0u, first % runs};  // consumed
+    if (cp.row > nrows) cp.row = nrows;
+    Pos pp = cp;                                                  // next to stage
 #pragma unroll
     for (int st = 0; st < 2; ++st) {
-        if (lane == 0 && pi < ba.items) issue_tile(ba.planes, tile_of(pi, pu), &sbuf[warp][st][0], &sbar[warp][st]);
-        advance(pi, pu);
+        if (lane == 0 && pp.row < nrows) issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
+        advance(pp);
     }
 
-    for (uint64_t s = 0; ci < ba.items; ++s, advance(ci, cu)) {
+    for (uint64_t s = 0; cp.row < nrows; ++s, advance(cp)) {
         const int st = (int)(s & 1);
         const uint32_t par = (uint32_t)(s >> 1) & 1u;
-        const uint64_t item = ci, tile = tile_of(ci, cu);
+        const uint64_t tile = tile_of(cp);
         const bool ok = dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
         if (__any_sync(kFull, !ok)) {
             if (lane == 0) {
                 atomicOr(ba.status, kDevTimeout);
                 // let the copies this warp still has in flight land before it leaves
                 dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
-                uint64_t ni = ci;
-                uint32_t nu = cu;
-                advance(ni, nu);
-                if (ni < ba.items)
+                Pos nq = cp;
+                advance(nq);
+                if (nq.row < nrows)
                     dev::mbar_wait_bounded(&sbar[warp][st ^ 1], (uint32_t)((s + 1) >> 1) & 1u, kWaitLimitNs);
             }
             return;
@@ -296,7 +314,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
         // the tile stays staged until the item is done: evaluations read
         // their blocks from it when they need them
         const uint2 *stage = &sbuf[warp][st][0];
-        const uint2 ph = __ldg(ba.phases + item / ba.runs);
+        const uint2 ph = __ldg(ba.phases + cp.row);
         for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
             const uint32_t pfirst = grp * kP;
             const uint32_t gk = __ldg(ba.gkind + grp);
@@ -321,9 +339,11 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
                     }
                 }
             } else if (kind == kKindShort) {
-                short_group<1>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                if (cnt == kP) short_group<1, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                else short_group<1, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
             } else if (kind == kKindShort2) {
-                short_group<2>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                if (cnt == kP) short_group<2, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                else short_group<2, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
             } else {
                 // ---- window-sliced group: one pattern at a time over all groups ----
                 for (uint32_t i = 0; i < cnt; ++i) {
@@ -367,11 +387,11 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
         }  // groups of the item
         // the tile is done: refill its stage with sequence position s + 2
         __syncwarp();
-        if (lane == 0 && pi < ba.items) {
+        if (lane == 0 && pp.row < nrows) {
             dev::fence_proxy_async_smem();
-            issue_tile(ba.planes, tile_of(pi, pu), &sbuf[warp][st][0], &sbar[warp][st]);
+            issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
         }
-        advance(pi, pu);
+        advance(pp);
     }
 }
 
@@ -406,46 +426,57 @@ int batched_grid(int device, int ws_max)
 }  // namespace
 }  // namespace pm
 
-using namespace pm;
+namespace pm {
+namespace {
 
-extern "C" {
+// Everything pm_batch_create works out on the host before touching the device.
+struct BatchPlan {
+    std::vector<PatDesc> desc;
+    std::vector<uint4> arena;
+    std::vector<uint32_t> order, gkind;
+    std::vector<uint2> phases;
+    int ws_max = -1;
+    int grid = 0;
+    uint32_t tiles = 1;
+    uint64_t ntiles = 0, runs = 0;
+    int key_bits = 0;
+};
 
-pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
-                          const int32_t *k, uint64_t capacity, const pm_batch_options *opts,
-                          void *stream, pm_batch **out)
+pm_status check_pairs(const char *who, const pm_text *text, const pm_pattern *const *patterns,
+                      uint32_t npat, const int32_t *k, uint64_t capacity, int *dev)
 {
-    if (!text || !out || (npat > 0 && (!patterns || !k))) {
-        set_error("pm_batch_create: NULL argument");
-        return PM_E_ARG;
-    }
-    *out = nullptr;
     if (npat == 0 || npat > PM_MAX_BATCH || capacity > kMaxCapacity) {
-        set_error("pm_batch_create: npat = %u (1..%u), capacity %llu (<= %llu)", npat, PM_MAX_BATCH,
+        set_error("%s: npat = %u (1..%u), capacity %llu (<= %llu)", who, npat, PM_MAX_BATCH,
                   (unsigned long long)capacity, (unsigned long long)kMaxCapacity);
         return npat == 0 ? PM_E_ARG : PM_E_TOO_LARGE;
     }
     for (uint32_t p = 0; p < npat; ++p) {
         if (!patterns[p] || k[p] < 0) {
-            set_error("pm_batch_create: pattern %u is NULL or has k < 0", p);
+            set_error("%s: pattern %u is NULL or has k < 0", who, p);
             return PM_E_ARG;
         }
     }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev != text->device) {
-        set_error("pm_batch_create: text lives on device %d, current device is %d", text->device, dev);
+    cudaGetDevice(dev);
+    if (*dev != text->device) {
+        set_error("%s: text lives on device %d, current device is %d", who, text->device, *dev);
         return PM_E_ARG;
     }
+    return PM_OK;
+}
+
+pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *const *patterns,
+                     uint32_t npat, const int32_t *k, const pm_batch_options *opts, int dev,
+                     BatchPlan &pl)
+{
     const pm_batch_options o = opts ? *opts : pm_batch_options{};
     auto below_ok = [](int32_t v, int32_t hi) { return v >= -1 && v <= hi; };
     if (o.group < 0 || o.grid < 0 || o.tiles < 0 || o.tiles > kMaxTilesPerItem ||
         !below_ok(o.ws_below, kWsMaxK + 1) || !below_ok(o.ps1_below, 32) || !below_ok(o.ps2_below, 64)) {
-        set_error("pm_batch_create: options out of range (group %d, grid %d, tiles %d, ws_below %d, "
-                  "ps1_below %d, ps2_below %d)", o.group, o.grid, o.tiles, o.ws_below, o.ps1_below,
+        set_error("%s: options out of range (group %d, grid %d, tiles %d, ws_below %d, "
+                  "ps1_below %d, ps2_below %d)", who, o.group, o.grid, o.tiles, o.ws_below, o.ps1_below,
                   o.ps2_below);
         return PM_E_ARG;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // Defaults, measured on GB300 (3.1 Gbp text, 64 pairs of m 32..1024):
     // the window-sliced counter while few positions decide a window (k <= 4),
     // then pattern-sliced groups with shared shifts over one chunk while the
@@ -456,12 +487,15 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
     const int ps1_max = below(o.ps1_below, 18) - 1;
     const int ps2_max = below(o.ps2_below, 41) - 1;
     const uint32_t tiles = o.tiles > 0 ? (uint32_t)o.tiles : 1u;
-    const uint32_t groups_per_row = o.group > 0 ? (uint32_t)((o.group + kP - 1) / kP) : UINT32_MAX;
+    // rows of 2 groups by default: measured faster than whole categories for
+    // the pattern-sliced kinds (k = 16..31: 4-20 %), equal for the others
+    const uint32_t groups_per_row = o.group > 0 ? (uint32_t)((o.group + kP - 1) / kP) : 2u;
 
-    // descriptors and arena (host side first)
-    std::vector<PatDesc> desc(npat);
+    // descriptors and arena
+    std::vector<PatDesc> &desc = pl.desc;
+    desc.assign(npat, PatDesc{});
     std::unordered_map<const pm_pattern *, std::pair<uint64_t, uint64_t>> where;
-    std::vector<uint4> arena;
+    std::vector<uint4> &arena = pl.arena;
     uint32_t min_m = UINT32_MAX;
     for (uint32_t p = 0; p < npat; ++p) {
         const pm_pattern *pt = patterns[p];
@@ -512,8 +546,6 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
                                                          : kWsMaxK + 3;
         cats[c].push_back(p);
     }
-    std::vector<uint32_t> order, gkind;
-    std::vector<uint2> phases;
     // gkind: bits 0-1 the kind, bits 2.. the number of real pairs (the last
     // group of a category is padded to kP slots with repeats of its first
     // pair; padding is never emitted)
@@ -525,107 +557,108 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
                               : c == (size_t)kWsMaxK + 1 ? kKindShort
                               : c == (size_t)kWsMaxK + 2 ? kKindShort2
                                                          : kKindLong;
-        const uint32_t g0 = (uint32_t)gkind.size();
+        const uint32_t g0 = (uint32_t)pl.gkind.size();
         for (size_t i = 0; i < v.size(); i += kP) {
             const uint32_t count = (uint32_t)std::min<size_t>(kP, v.size() - i);
-            for (size_t j = i; j < i + kP; ++j) order.push_back(j < v.size() ? v[j] : v[i]);
-            gkind.push_back(kind | (count << 2));
+            for (size_t j = i; j < i + kP; ++j) pl.order.push_back(j < v.size() ? v[j] : v[i]);
+            pl.gkind.push_back(kind | (count << 2));
         }
-        const uint32_t g1 = (uint32_t)gkind.size();
+        const uint32_t g1 = (uint32_t)pl.gkind.size();
         for (uint32_t r = g0; r < g1; r += std::min(groups_per_row, g1 - r))
-            phases.push_back(make_uint2(r, r + std::min(groups_per_row, g1 - r)));
+            pl.phases.push_back(make_uint2(r, r + std::min(groups_per_row, g1 - r)));
     }
-    const uint32_t ngroups = (uint32_t)gkind.size();
-
-    pm_batch *b = new (std::nothrow) pm_batch{};
-    if (!b) return PM_E_NOMEM;
-    b->device = dev;
-    b->npat = npat;
-    b->ngroups = ngroups;
-    b->ws_max = ws_max;
-    b->grid = o.grid > 0 ? o.grid : batched_grid(dev, ws_max);
-    b->ntiles = min_m <= text->n ? (text->n - min_m + 1 + kTileWindows - 1) / kTileWindows : 0;
-    b->tiles = tiles;
-    b->runs = (b->ntiles + tiles - 1) / tiles;
-    b->nphases = (uint32_t)phases.size();
-    b->capacity = capacity;
-    b->planes = text->planes;
-    b->unk = text->unk;
-    const unsigned long long max_key = (unsigned long long)npat * (b->ntiles ? b->ntiles : 1) * G;
-    b->key_bits = 0;
-    while (b->key_bits < 64 && (max_key >> b->key_bits) != 0) ++b->key_bits;
-
-    const uint64_t cap_e = capacity ? capacity : 1;
-    const size_t sz_pats = align256(npat * sizeof(PatDesc));
-    const size_t sz_order = align256(order.size() * sizeof(uint32_t));
-    const size_t sz_gkind = align256(gkind.size() * sizeof(uint32_t));
-    const size_t sz_phases = align256(std::max<size_t>(phases.size(), 1) * sizeof(uint2));
-    const size_t sz_arena = align256(arena.size() * sizeof(uint4));
-    const size_t sz_tmp = align256(cap_e * sizeof(pm_hit));
-    const size_t sz_recs = align256(cap_e * sizeof(SegRecord));
-    const size_t sz_sort = align256(sort_scratch_bytes(cap_e));
-    const size_t sz_entries = align256(cap_e * sizeof(TileEntry));
-    const size_t sz_ordscr = align256(order_scratch_bytes(cap_e));
-    const size_t sz_ctl = 256;
-    const size_t sz_counts = align256(npat * sizeof(unsigned long long));
-    const size_t total = sz_pats + sz_order + sz_gkind + sz_phases + sz_arena + sz_tmp + sz_recs +
-                         sz_sort + sz_entries + sz_ordscr + sz_ctl + sz_counts;
-    pm_status rc = cuda_status(cudaMalloc(&b->mem, total), "cudaMalloc batch");
-    if (rc) {
-        delete b;
-        return rc;
-    }
-    char *c = (char *)b->mem;
-    auto take = [&](size_t n) { char *r = c; c += n; return (void *)r; };
-    b->pats = (PatDesc *)take(sz_pats);
-    b->order = (uint32_t *)take(sz_order);
-    b->gkind = (uint32_t *)take(sz_gkind);
-    b->phases = (uint2 *)take(sz_phases);
-    b->arena = (uint4 *)take(sz_arena);
-    b->tmp = (pm_hit *)take(sz_tmp);
-    b->recs = (SegRecord *)take(sz_recs);
-    b->sort_scratch = take(sz_sort);
-    b->entries = (TileEntry *)take(sz_entries);
-    b->order_scratch = take(sz_ordscr);
-    b->ctl = (unsigned long long *)take(sz_ctl);
-    b->pat_counts = (unsigned long long *)take(sz_counts);
-    rc = cuda_status(cudaMemcpyAsync(b->pats, desc.data(), npat * sizeof(PatDesc),
-                                     cudaMemcpyHostToDevice, st), "upload descriptors");
-    if (!rc)
-        rc = cuda_status(cudaMemcpyAsync(b->order, order.data(), order.size() * sizeof(uint32_t),
-                                         cudaMemcpyHostToDevice, st), "upload groups");
-    if (!rc)
-        rc = cuda_status(cudaMemcpyAsync(b->gkind, gkind.data(), gkind.size() * sizeof(uint32_t),
-                                         cudaMemcpyHostToDevice, st), "upload group kinds");
-    if (!rc && !phases.empty())
-        rc = cuda_status(cudaMemcpyAsync(b->phases, phases.data(), phases.size() * sizeof(uint2),
-                                         cudaMemcpyHostToDevice, st), "upload phases");
-    if (!rc)
-        rc = cuda_status(cudaMemcpyAsync(b->arena, arena.data(), arena.size() * sizeof(uint4),
-                                         cudaMemcpyHostToDevice, st), "upload arena");
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
-    if (rc) {
-        cudaFree(b->mem);
-        delete b;
-        return rc;
-    }
-    *out = b;
+    pl.ws_max = ws_max;
+    pl.grid = o.grid > 0 ? o.grid : batched_grid(dev, ws_max);
+    pl.tiles = tiles;
+    pl.ntiles = min_m <= text->n ? (text->n - min_m + 1 + kTileWindows - 1) / kTileWindows : 0;
+    pl.runs = (pl.ntiles + tiles - 1) / tiles;
+    const unsigned long long max_key = (unsigned long long)npat * (pl.ntiles ? pl.ntiles : 1) * G;
+    pl.key_bits = 0;
+    while (pl.key_bits < 64 && (max_key >> pl.key_bits) != 0) ++pl.key_bits;
     return PM_OK;
 }
 
-pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *stream)
+// Lay the batch's device data out from `base` (nullptr: only size it).
+// Returns the bytes needed.
+size_t carve_batch(const BatchPlan &pl, uint32_t npat, uint64_t capacity, pm_batch *b, char *base)
 {
-    if (!b || !offsets || (b->capacity > 0 && !hits)) {
-        set_error("pm_batch_run: NULL argument");
-        return PM_E_ARG;
-    }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev != b->device) {
-        set_error("pm_batch_run: batch lives on device %d, current device is %d", b->device, dev);
-        return PM_E_ARG;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t cap_e = capacity ? capacity : 1;
+    const size_t sz[] = {
+        align256(npat * sizeof(PatDesc)),
+        align256(pl.order.size() * sizeof(uint32_t)),
+        align256(pl.gkind.size() * sizeof(uint32_t)),
+        align256(std::max<size_t>(pl.phases.size(), 1) * sizeof(uint2)),
+        align256(pl.arena.size() * sizeof(uint4)),
+        align256(cap_e * sizeof(pm_hit)),
+        align256(cap_e * sizeof(SegRecord)),
+        align256(sort_scratch_bytes(cap_e)),
+        align256(cap_e * sizeof(TileEntry)),
+        align256(order_scratch_bytes(cap_e)),
+        256,
+        align256(npat * sizeof(unsigned long long)),
+    };
+    size_t total = 0;
+    for (size_t x : sz) total += x;
+    if (!base) return total;
+    char *c = base;
+    auto take = [&](size_t i) { char *r = c; c += sz[i]; return (void *)r; };
+    b->pats = (PatDesc *)take(0);
+    b->order = (uint32_t *)take(1);
+    b->gkind = (uint32_t *)take(2);
+    b->phases = (uint2 *)take(3);
+    b->arena = (uint4 *)take(4);
+    b->tmp = (pm_hit *)take(5);
+    b->recs = (SegRecord *)take(6);
+    b->sort_scratch = take(7);
+    b->entries = (TileEntry *)take(8);
+    b->order_scratch = take(9);
+    b->ctl = (unsigned long long *)take(10);
+    b->pat_counts = (unsigned long long *)take(11);
+    return total;
+}
+
+void fill_batch(const BatchPlan &pl, const pm_text *text, uint32_t npat, uint64_t capacity, int dev,
+                pm_batch *b)
+{
+    b->device = dev;
+    b->npat = npat;
+    b->ngroups = (uint32_t)pl.gkind.size();
+    b->ws_max = pl.ws_max;
+    b->grid = pl.grid;
+    b->ntiles = pl.ntiles;
+    b->tiles = pl.tiles;
+    b->runs = pl.runs;
+    b->nphases = (uint32_t)pl.phases.size();
+    b->capacity = capacity;
+    b->planes = text->planes;
+    b->unk = text->unk;
+    b->key_bits = pl.key_bits;
+}
+
+// Copies from pageable host memory are staged by the driver: the plan may be
+// destroyed as soon as these calls return.
+pm_status upload_batch(const BatchPlan &pl, pm_batch *b, cudaStream_t st)
+{
+    pm_status rc = cuda_status(cudaMemcpyAsync(b->pats, pl.desc.data(), b->npat * sizeof(PatDesc),
+                                               cudaMemcpyHostToDevice, st), "upload descriptors");
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(b->order, pl.order.data(), pl.order.size() * sizeof(uint32_t),
+                                         cudaMemcpyHostToDevice, st), "upload groups");
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(b->gkind, pl.gkind.data(), pl.gkind.size() * sizeof(uint32_t),
+                                         cudaMemcpyHostToDevice, st), "upload group kinds");
+    if (!rc && !pl.phases.empty())
+        rc = cuda_status(cudaMemcpyAsync(b->phases, pl.phases.data(), pl.phases.size() * sizeof(uint2),
+                                         cudaMemcpyHostToDevice, st), "upload rows");
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(b->arena, pl.arena.data(), pl.arena.size() * sizeof(uint4),
+                                         cudaMemcpyHostToDevice, st), "upload arena");
+    return rc;
+}
+
+// The persistent launch plus the ordering kernels into device buffers.
+pm_status run_batch(const pm_batch *b, pm_hit *hits, uint64_t *offsets, cudaStream_t st)
+{
     unsigned long long *cursor = b->ctl, *rec_cursor = b->ctl + 1;
     uint32_t *status = (uint32_t *)(b->ctl + 2);
     pm_status rc = cuda_status(cudaMemsetAsync(b->ctl, 0, 256, st), "clear control words");
@@ -661,6 +694,88 @@ pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *strea
                                               b->order_scratch, st),
                          "order kernels");
     return rc;
+}
+
+}  // namespace
+
+pm_status search_batched(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                         const int32_t *k, uint64_t capacity, const pm_batch_options *opts,
+                         pm_hit *d_hits, uint64_t *d_offsets, void **scratch, cudaStream_t st)
+{
+    *scratch = nullptr;
+    int dev = 0;
+    pm_status rc = check_pairs("pm_search (batched)", text, patterns, npat, k, capacity, &dev);
+    if (rc) return rc;
+    BatchPlan pl;
+    rc = plan_batch("pm_search (batched)", text, patterns, npat, k, opts, dev, pl);
+    if (rc) return rc;
+    pm_batch b{};
+    fill_batch(pl, text, npat, capacity, dev, &b);
+    const size_t total = carve_batch(pl, npat, capacity, &b, nullptr);
+    rc = cuda_status(cudaMallocAsync(scratch, total, st), "cudaMallocAsync batch scratch");
+    if (rc) return rc;
+    carve_batch(pl, npat, capacity, &b, (char *)*scratch);
+    rc = upload_batch(pl, &b, st);
+    if (!rc) rc = run_batch(&b, d_hits, d_offsets, st);
+    return rc;
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                          const int32_t *k, uint64_t capacity, const pm_batch_options *opts,
+                          void *stream, pm_batch **out)
+{
+    if (!text || !out || (npat > 0 && (!patterns || !k))) {
+        set_error("pm_batch_create: NULL argument");
+        return PM_E_ARG;
+    }
+    *out = nullptr;
+    int dev = 0;
+    pm_status rc = check_pairs("pm_batch_create", text, patterns, npat, k, capacity, &dev);
+    if (rc) return rc;
+    BatchPlan pl;
+    rc = plan_batch("pm_batch_create", text, patterns, npat, k, opts, dev, pl);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    pm_batch *b = new (std::nothrow) pm_batch{};
+    if (!b) return PM_E_NOMEM;
+    fill_batch(pl, text, npat, capacity, dev, b);
+    const size_t total = carve_batch(pl, npat, capacity, b, nullptr);
+    rc = cuda_status(cudaMalloc(&b->mem, total), "cudaMalloc batch");
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    carve_batch(pl, npat, capacity, b, (char *)b->mem);
+    rc = upload_batch(pl, b, st);
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
+    if (rc) {
+        cudaFree(b->mem);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PM_OK;
+}
+
+pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *stream)
+{
+    if (!b || !offsets || (b->capacity > 0 && !hits)) {
+        set_error("pm_batch_run: NULL argument");
+        return PM_E_ARG;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != b->device) {
+        set_error("pm_batch_run: batch lives on device %d, current device is %d", b->device, dev);
+        return PM_E_ARG;
+    }
+    return run_batch(b, hits, offsets, (cudaStream_t)stream);
 }
 
 uint64_t pm_batch_capacity(const pm_batch *b) { return b ? b->capacity : 0; }

@@ -142,6 +142,14 @@ enum class Variant : int {
 // becomes kAllChunks.
 Variant resolve_variant(Variant v, int32_t k);
 
+// pm_search_ex's one-launch path (pm_batch.cu): plans the pairs as
+// pm_batch_create does, takes all scratch from the stream-ordered pool
+// (*scratch, to be freed on the stream by the caller, also on error) and
+// queues the batched launch and ordering into the device outputs.
+pm_status search_batched(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                         const int32_t *k, uint64_t capacity, const pm_batch_options *opts,
+                         pm_hit *d_hits, uint64_t *d_offsets, void **scratch, cudaStream_t st);
+
 // Launch one scan kernel for one pattern (pm_scan.cu).
 cudaError_t launch_scan(Variant v, const uint2 *planes, const uint32_t *unk, const PatDesc &d,
                         const uint4 *arena, TileEntry *table, pm_hit *tmp, uint64_t cap,

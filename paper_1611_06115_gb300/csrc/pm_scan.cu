@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
         if (__any_sync(kFull, anyp != 0u)) {
             uint32_t total;
             unsigned long long base;
-            emit_tile_hits(pass, blk, d, M, planes, unk, tmp, cap, cursor, total, base);
+            emit_tile_hits<kLateRefill>(pass, blk, a, b, M0, d, M, planes, unk, tmp, cap, cursor, total,
+                                        base);
             if (lane == 0) table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
         } else if (lane == 0) {
             table[d.tile0 + tile] = TileEntry{0u, 0u};

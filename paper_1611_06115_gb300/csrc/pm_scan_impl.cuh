@@ -389,7 +389,15 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
 // warp-aggregated atomic on cursor.  Call with the whole warp and only when
 // some lane has a pass bit.  Returns (on every lane) the number of hits and
 // where they start in tmp.
+// kRegs: the lane's blocks a[g], b[g] (registers) and the chunk-0 masks M0
+// give the first 32 positions of a hit's count without a memory access
+// (deeper chunks, and texts with unknown symbols, count through L1/L2); used
+// by the pattern-sliced kernels, whose hits are dense for small m and large
+// k.  Otherwise every hit is counted through L1/L2, which keeps a and b out
+// of registers during emission.
+template <bool kRegs>
 __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64_t (&blk)[G],
+                                               const uint2 (&a)[G], const uint2 (&b)[G], uint4 M0,
                                                const PatDesc &d, const uint4 *__restrict__ M,
                                                const uint2 *__restrict__ planes,
                                                const uint32_t *__restrict__ unk,
@@ -429,8 +437,15 @@ __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64
             const uint32_t w = __ffs(hm) - 1;
             hm &= hm - 1;
             if (q < cap) {
-                const uint32_t c = window_count_exact(planes, unk, blk[g], w, M, d.nchunks,
-                                                      (uint32_t)d.k);
+                uint32_t c;
+                if (!kRegs || unk) {
+                    c = window_count_exact(planes, unk, blk[g], w, M, d.nchunks, (uint32_t)d.k);
+                } else {
+                    c = __popc(~class_match(__funnelshift_r(a[g].x, b[g].x, w),
+                                            __funnelshift_r(a[g].y, b[g].y, w), M0));
+                    if (d.nchunks > 1)
+                        c = window_count_from(planes, blk[g], w, M, 1, d.nchunks, c, (uint32_t)d.k);
+                }
                 tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
             }
             ++q;

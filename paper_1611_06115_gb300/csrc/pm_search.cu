@@ -67,6 +67,81 @@ void release_pinned(PinnedSlot *s, cudaStream_t st)
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Reads the total (and, for host outputs, the results) back when the caller
+// asked for them; shared tail of both search paths.
+pm_status finish_search(uint32_t npat, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                        uint64_t *needed, bool dev_out, const pm_hit *d_hits,
+                        const uint64_t *d_offsets, void *const *scratch, int nscratch,
+                        pm_status rc, cudaStream_t st)
+{
+    uint64_t total = 0;
+    bool waited = false;
+    if (!rc && !dev_out) {
+        rc = cuda_status(cudaMemcpyAsync(offsets, d_offsets, (npat + 1) * sizeof(uint64_t),
+                                         cudaMemcpyDeviceToHost, st),
+                         "copy offsets");
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
+        waited = true;
+        total = offsets[npat];
+        if (!rc && total != PM_TOTAL_ERROR && total <= capacity && total > 0) {
+            rc = cuda_status(cudaMemcpyAsync(hits, d_hits, total * sizeof(pm_hit),
+                                             cudaMemcpyDeviceToHost, st),
+                             "copy hits");
+        }
+    } else if (!rc && needed) {
+        rc = cuda_status(cudaMemcpyAsync(&total, d_offsets + npat, sizeof total,
+                                         cudaMemcpyDeviceToHost, st),
+                         "copy total");
+        waited = true;
+    }
+    for (int i = 0; i < nscratch; ++i)
+        if (scratch[i]) cudaFreeAsync(scratch[i], st);
+    if (waited) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (!rc) rc = cuda_status(e, "stream synchronize");
+    }
+    if (rc) return rc;
+    if (waited) {
+        if (total == PM_TOTAL_ERROR) {
+            set_error("pm_search: a device wait timed out");
+            return PM_E_TIMEOUT;
+        }
+        if (needed) *needed = total;
+        if (total > capacity) {
+            set_error("pm_search: %llu hits, capacity %llu", (unsigned long long)total,
+                      (unsigned long long)capacity);
+            return PM_E_OVERFLOW;
+        }
+    }
+    return PM_OK;
+}
+
+// pm_search_ex with options->batch: one persistent launch for all pairs.
+pm_status search_ex_batched(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,
+                            const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
+                            uint64_t *needed, bool dev_out, const pm_options &o, cudaStream_t st)
+{
+    if (o.events) {
+        set_error("pm_search: per-pattern events need one launch per pattern (options->batch is set)");
+        return PM_E_ARG;
+    }
+    void *scratch[2] = {nullptr, nullptr};
+    pm_hit *d_hits = hits;
+    uint64_t *d_offsets = offsets;
+    pm_status rc = PM_OK;
+    if (!dev_out) {  // host outputs: device buffers first
+        const size_t hb = align256((capacity ? capacity : 1) * sizeof(pm_hit));
+        rc = cuda_status(cudaMallocAsync(&scratch[1], hb + (npat + 1) * sizeof(uint64_t), st),
+                         "cudaMallocAsync outputs");
+        if (rc) return rc;
+        d_hits = (pm_hit *)scratch[1];
+        d_offsets = (uint64_t *)((char *)scratch[1] + hb);
+    }
+    rc = search_batched(text, patterns, npat, k, capacity, o.batch, d_hits, d_offsets, &scratch[0], st);
+    return finish_search(npat, hits, capacity, offsets, needed, dev_out, d_hits, d_offsets, scratch, 2,
+                         rc, st);
+}
+
 }  // namespace
 }  // namespace pm
 
@@ -115,6 +190,9 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                   (unsigned long long)kMaxCapacity);
         return PM_E_TOO_LARGE;
     }
+
+    if (o.batch && npat > 0) return search_ex_batched(text, patterns, npat, k, hits, capacity, offsets,
+                                                     needed, dev_out, o, st);
 
     // ---- descriptors and the arena (chunk masks, window-sliced lists) ----
     std::vector<PatDesc> desc(npat);
@@ -216,45 +294,9 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                                       d_offsets, d_status, d_order, st),
                          "order kernels");
 
-    uint64_t total = 0;
-    bool waited = false;
-    if (!rc && !dev_out) {
-        rc = cuda_status(cudaMemcpyAsync(offsets, d_offsets, (npat + 1) * sizeof(uint64_t),
-                                         cudaMemcpyDeviceToHost, st),
-                         "copy offsets");
-        if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
-        waited = true;
-        total = offsets[npat];
-        if (!rc && total != PM_TOTAL_ERROR && total <= capacity && total > 0) {
-            rc = cuda_status(cudaMemcpyAsync(hits, d_hits, total * sizeof(pm_hit),
-                                             cudaMemcpyDeviceToHost, st),
-                             "copy hits");
-        }
-    } else if (!rc && needed) {
-        rc = cuda_status(cudaMemcpyAsync(&total, d_offsets + npat, sizeof total,
-                                         cudaMemcpyDeviceToHost, st),
-                         "copy total");
-        waited = true;
-    }
-    cudaFreeAsync(scratch, st);
-    if (waited) {
-        const cudaError_t e = cudaStreamSynchronize(st);
-        if (!rc) rc = cuda_status(e, "stream synchronize");
-    }
-    if (rc) return rc;
-    if (waited) {
-        if (total == PM_TOTAL_ERROR) {
-            set_error("pm_search: a device wait timed out");
-            return PM_E_TIMEOUT;
-        }
-        if (needed) *needed = total;
-        if (total > capacity) {
-            set_error("pm_search: %llu hits, capacity %llu", (unsigned long long)total,
-                      (unsigned long long)capacity);
-            return PM_E_OVERFLOW;
-        }
-    }
-    return PM_OK;
+    void *const scr[1] = {scratch};
+    return finish_search(npat, hits, capacity, offsets, needed, dev_out, d_hits, d_offsets, scr, 1, rc,
+                         st);
 }
 
 pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint32_t npat,

@@ -5,7 +5,8 @@ a batch whenever a slot (a CUDA stream) is free and the batch's projected
 device memory fits the budget; batches are issued without waiting, so those
 in different slots run concurrently on the GPU, and queries that arrive
 while others run are admitted as soon as a slot and memory free up.  A batch
-mixes queries of any m and k (one search call, one scan launch per query).
+mixes queries of any m and k in one search call: one scan launch per query,
+or one persistent launch for the whole batch (``GpuBackend(batch=...)``).
 
 Memory admission uses a per-query projection of the output size: the
 expected number of windows with at most k mismatches, from a Poisson-
@@ -237,9 +238,11 @@ def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
 
 class GpuBackend:
     """Issues each batch as one asynchronous pm_search_ex call on its slot's
-    stream (device outputs, scratch from the stream-ordered pool)."""
+    stream (device outputs, scratch from the stream-ordered pool): one scan
+    launch per query, or with ``batch`` (batch options, {} for defaults) one
+    persistent launch for the whole batch."""
 
-    def __init__(self, text, slots: int = 3, copy_to_host: bool = False):
+    def __init__(self, text, slots: int = 3, copy_to_host: bool = False, batch: dict | None = None):
         import torch
         from . import api
         self.api = api
@@ -247,6 +250,7 @@ class GpuBackend:
         self.text = text
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.copy_to_host = copy_to_host
+        self.batch = batch
         self._compiled: dict[str, object] = {}
 
     def _pattern(self, p: str):
@@ -256,9 +260,10 @@ class GpuBackend:
             self._compiled[p] = c
         return c
 
-    @staticmethod
-    def bytes_for(reqs, n: int) -> int:
+    def bytes_for(self, reqs, n: int) -> int:
         cap = sum(r.capacity for r in reqs)
+        if self.batch is not None:  # hits, records, sort and ordering scratch
+            return 64 * cap + 4096 * len(reqs) + (1 << 20)
         tiles = sum((max(n - len(r.pattern) + 1, 0) + 4095) // 4096 for r in reqs)
         return 16 * cap + 24 * tiles + 4096 * len(reqs)
 
@@ -268,7 +273,8 @@ class GpuBackend:
         cap = sum(r.capacity for r in reqs)
         with torch.cuda.stream(st):
             res = self.api.pm_search_ex(self.text, [self._pattern(r.pattern) for r in reqs],
-                                        [r.k for r in reqs], capacity=cap, stream=st, sync=False)
+                                        [r.k for r in reqs], capacity=cap, stream=st, sync=False,
+                                        batch=self.batch)
             ev = torch.cuda.Event()
             ev.record(st)
         return (res, ev, cap)

@@ -43,11 +43,11 @@ BATCH_SPACE = (
     ("ws_below", (1, 3, 5, 7)),
     ("ps1_below", (12, 15, 18, 21, 24)),
     ("ps2_below", (33, 37, 41, 45, 49)),
-    ("group", (0, 64, 256)),
+    ("group", (8, 16, 64, 256, 1 << 16)),
     ("tiles", (1, 2, 4)),
     ("grid", (0,)),  # extended at run time with fractions of the resident grid
 )
-BATCH_DEFAULTS = {"ws_below": 5, "ps1_below": 18, "ps2_below": 41, "group": 0, "tiles": 1, "grid": 0}
+BATCH_DEFAULTS = {"ws_below": 5, "ps1_below": 18, "ps2_below": 41, "group": 16, "tiles": 1, "grid": 0}
 
 
 def valid_variants(k: int) -> list[int]:

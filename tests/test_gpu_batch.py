@@ -162,3 +162,39 @@ def test_autotuner_on_device(pm, tmp_path):
     finally:
         pm.pm_set_auto_variants([])
     assert pm.pm_get_auto_variants() == builtin
+
+
+def test_search_ex_one_launch_equals_per_pattern(pm):
+    """pm_search_ex with batch options: one persistent launch, stream-ordered
+    scratch; same hits as one launch per pattern, for device and host
+    outputs, with `needed` and an overflow."""
+    import torch
+    rng = np.random.default_rng(71)
+    text = synth.markov_text(3 * 4096 * 32 + 501, seed=71)
+    t = pm.pm_encode_text(text)
+    pats = [synth.random_pattern(int(m), int(m) // 10, rng)
+            for m in rng.choice([8, 20, 33, 64, 150, 400], size=40)]
+    ks = [int(x) for x in rng.integers(0, 12, size=40)]
+    cps = [pm.pm_compile_pattern(p) for p in pats]
+    ref = pm.pm_search(t, cps, ks)
+    check_against_oracle(ref, text, pats, ks)
+    for opts in ({}, {"ws_below": -1, "tiles": 2}, {"ps1_below": 3, "group": 16}):
+        got = pm.pm_search_ex(t, cps, ks, batch=opts)
+        assert got.total == ref.total
+        assert np.array_equal(got.numpy()[0], ref.numpy()[0])
+        assert np.array_equal(got.numpy()[1], ref.numpy()[1])
+        host = pm.pm_search_ex(t, cps, ks, out="host", batch=opts)
+        assert np.array_equal(host.numpy()[0], ref.numpy()[0])
+        asyn = pm.pm_search_ex(t, cps, ks, capacity=ref.total, sync=False, batch=opts)
+        torch.cuda.synchronize()
+        assert asyn.total == ref.total and np.array_equal(asyn.numpy()[0], ref.numpy()[0])
+    # too small a capacity: the library reports the count it needs
+    small = pm.pm_search_ex(t, cps, ks, batch={}, capacity=None)
+    assert small.total == ref.total
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_search_ex(t, cps, ks, batch={}, capacity=max(ref.total // 2, 1), out="host")
+    assert e.value.status == pm.PM_E_OVERFLOW
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(cps))]
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_search_ex(t, cps, ks, batch={}, events=ev)
+    assert e.value.status == pm.PM_E_ARG

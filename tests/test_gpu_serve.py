@@ -10,7 +10,8 @@ from synth import workloads
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_solo_searches():
+@pytest.mark.parametrize("batch", (None, {}), ids=("launch-per-query", "one-launch-per-batch"))
+def test_served_results_equal_solo_searches(batch):
     import torch
     import paper_1611_06115_gb300 as pm
     from paper_1611_06115_gb300 import serve
@@ -20,7 +21,7 @@ def test_served_results_equal_solo_searches():
     # a burst: arrivals outpace the device, so batches queue and overlap
     qs = workloads.serving_queries(rate=20000.0, duration=0.01, seed=32, hi=600)
     queries = [(q.arrival, q.pattern, q.k) for q in qs]
-    backend = serve.GpuBackend(text, slots=3)
+    backend = serve.GpuBackend(text, slots=3, batch=batch)
     srv = serve.Server(backend, n=text.n, slots=3, max_batch=8, mem_budget=4 << 30)
     stats = serve.run_trace(srv, queries)
     torch.cuda.synchronize()
