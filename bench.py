@@ -74,7 +74,7 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--variant", type=int, default=0)
-    ap.add_argument("--workload", choices=("genome", "batched", "serving", "profile"),
+    ap.add_argument("--workload", choices=("genome", "batched", "serving", "large", "profile"),
                     default="genome",
                     help="genome (the default line); batched and serving print their own "
                          "lines; profile runs four single searches for an ncu capture")
@@ -623,6 +623,49 @@ def run_serving(a):
     print(json.dumps(stats), flush=True)
 
 
+def run_large(a):
+    """LARGE: the 3.1 Gbp Markov text, patterns m in {1e4, 1e5} with 5 % class
+    positions and 10 planted copies each (s uniform in 0..500), k in {0, 100,
+    1000}: kernel time per search (CUDA events around the scan launch) and
+    the whole pm_search call; every planted copy with s <= k must be found
+    with its exact count."""
+    import torch
+    import paper_1611_06115_gb300 as pm
+    from synth import workloads
+    n = a.n
+    host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    w = workloads.large(n=n, out=host.numpy())
+    text = pm.pm_encode_text(host)
+    del host
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for e in ev:
+        e.record(st)
+    rows = []
+    for p, pl in zip(w.patterns, w.planted):
+        c = pm.pm_compile_pattern(p)
+        for k in w.meta["ks"]:
+            best_k, best_call = float("inf"), float("inf")
+            for rep in range(max(a.steps, 1) + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = pm.pm_search_ex(text, [c], [k], events=ev)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if rep:
+                    best_k = min(best_k, ev[0].elapsed_time(ev[1]) / 1e3)
+                    best_call = min(best_call, dt)
+            found = dict(zip(*[x.tolist() for x in r.pattern(0)]))
+            ok = all(found.get(loc) == s for loc, s in pl if s <= k)
+            if not ok:
+                raise SystemExit(f"LARGE: planted copy missed for m={len(p)} k={k}")
+            cells = (n - len(p) + 1) * len(p)
+            rows.append({"m": len(p), "k": k, "kernel_s": best_k, "call_s": best_call,
+                         "hits": r.total, "window_cells_per_s": cells / best_k})
+    print(json.dumps({"workload": "LARGE", "metric": METRIC, "n": n, "searches": rows,
+                      "planted_found": True}), flush=True)
+
+
 def run_profile(a):
     """Five single searches of the GENOME m = 128 pattern over the first n
     symbols, one per kernel kind, for a small ncu capture:
@@ -646,6 +689,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "profile":
         run_profile(a)
+    elif a.workload == "large":
+        run_large(a)
     elif a.workload == "batched":
         run_batched(a)
     elif a.workload == "serving":
