@@ -74,8 +74,10 @@ typedef struct pm_batch pm_batch;     /* patterns + k + scratch, resident on the
  *         symbols per 32-bit word, 2 bits per symbol in total.
  *
  * The call returns after the coding has finished (it synchronises the
- * stream to check the symbols).  Host input is copied in pieces through a
- * device staging buffer, so the ASCII text never has to fit on the device.
+ * stream to check the symbols).  Page-locked host input (cudaHostAlloc,
+ * torch pin_memory) is read by the coding kernel in place over the host
+ * link; other host input is copied in pieces through a device staging
+ * buffer.  Either way the ASCII text never has to fit on the device.
  */
 pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **out);
 

@@ -146,6 +146,19 @@ bool is_device_pointer(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory (mapped into the device's
+// address space by unified addressing), or NULL for any other pointer.
+const char *pinned_device_view(const char *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (const char *)a.devicePointer : nullptr;
+}
+
 cudaError_t launch_pack(const char *ascii, uint64_t n_chunk, uint64_t first_symbol, uint2 *planes,
                         uint32_t *unk, unsigned long long *bad, cudaStream_t stream)
 {
@@ -218,6 +231,9 @@ pm_status pm_encode_text_ex(const char *ascii, uint64_t n, uint32_t flags, void 
     unsigned long long *bad = nullptr;  // [0] first bad offset, [1..3] C, G, T, [4] unknown counts
     char *staging = nullptr;
     const bool on_device = is_device_pointer(ascii);
+    // page-locked host input is read by the coding kernel in place (over the
+    // host link, no staging copy); other host memory is staged in pieces
+    const char *pinned = on_device ? nullptr : pinned_device_view(ascii);
     const uint64_t body = (n + 31) / 32;
     rc = cuda_status(cudaMemsetAsync(t->planes + body, 0, (t->nblocks - body) * sizeof(uint2), st),
                      "memset padding");
@@ -227,8 +243,9 @@ pm_status pm_encode_text_ex(const char *ascii, uint64_t n, uint32_t flags, void 
     if (!rc) rc = cuda_status(cudaMallocAsync((void **)&bad, 5 * sizeof *bad, st), "cudaMallocAsync");
     if (!rc) rc = cuda_status(cudaMemsetAsync(bad, 0xff, sizeof *bad, st), "memset");
     if (!rc) rc = cuda_status(cudaMemsetAsync(bad + 1, 0, 4 * sizeof *bad, st), "memset");
-    if (!rc && on_device) {
-        rc = cuda_status(launch_pack(ascii, n, 0, t->planes, t->unk, bad, st), "pack kernel");
+    if (!rc && (on_device || pinned)) {
+        rc = cuda_status(launch_pack(on_device ? ascii : pinned, n, 0, t->planes, t->unk, bad, st),
+                         "pack kernel");
     } else if (!rc && n > 0) {
         const uint64_t chunk = n < kHostChunk ? n : kHostChunk;
         rc = cuda_status(cudaMallocAsync((void **)&staging, (chunk + 15) & ~15ull, st),
