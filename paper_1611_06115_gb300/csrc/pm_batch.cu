@@ -363,21 +363,24 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
                     }
                     if (!__any_sync(kFull, anyv != 0u)) continue;
                     const uint4 *list = ba.arena + d.wslist;
+                    bool cut;
                     // only the thresholds this batch uses are compiled in (instruction cache)
-                    if (d.k == 0) alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else if (WSMAX >= 1 && d.k == 1) alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else if (WSMAX >= 2 && d.k == 2) alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else if (WSMAX >= 3 && d.k == 3) alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else if (WSMAX >= 4 && d.k == 4) alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else if (WSMAX >= 5 && d.k == 5) alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
-                    else alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, valid, pass);
+                    if (d.k == 0) cut = alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, ws_cut(0), valid, pass);
+                    else if (WSMAX >= 1 && d.k == 1) cut = alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 1 ? 1 : 0)), valid, pass);
+                    else if (WSMAX >= 2 && d.k == 2) cut = alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 2 ? 2 : 0)), valid, pass);
+                    else if (WSMAX >= 3 && d.k == 3) cut = alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 3 ? 3 : 0)), valid, pass);
+                    else if (WSMAX >= 4 && d.k == 4) cut = alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 4 ? 4 : 0)), valid, pass);
+                    else if (WSMAX >= 5 && d.k == 5) cut = alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 5 ? 5 : 0)), valid, pass);
+                    else cut = alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 6 ? 6 : 0)), valid, pass);
                     const uint4 *M = ba.arena + d.masks;
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         const uint32_t ps = d.nchunks > 1
                             ? settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M,
                                             d.nchunks, (uint32_t)d.k, ba.planes)
-                            : pass[g];
+                            : cut ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, (uint32_t)d.k,
+                                                     ba.planes)
+                                  : pass[g];
                         if (__any_sync(kFull, ps != 0u))
                             emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
                                        d.nchunks, (uint32_t)d.k, M, ba);

@@ -145,14 +145,27 @@ __device__ __forceinline__ uint4 ld_list(const uint4 *p)
     else return *p;
 }
 
+// List entries the window-sliced scan tests before it leaves the remaining
+// candidates to exact one-by-one counts (checked every four entries).
+// Measured on GB300 over a 3.1 Gbp text (m = 32 .. 1024): K = 0 8 entries
+// (2-3 % faster than no cut), K = 1..4 4 + 2K (7, 18, 4, 12 % faster); a
+// cut one block earlier leaves so many candidates that their serial counts
+// cost 1.4-4x the scan.
+__host__ __device__ constexpr uint32_t ws_cut(int K) { return K == 0 ? 8u : 4u + 2u * (uint32_t)K; }
+
 // Window-sliced first chunk with a thermometer counter of K+1 levels over the
 // listed positions, for all groups of the lane at once.  alive[g] receives
-// the windows still at or below K.
+// the windows still at or below K.  After `cut` list entries (checked every
+// four) the scan stops if some window is still alive and returns true: the
+// few candidates left are cheaper to count one by one (settle_from_regs)
+// than to carry the whole tile through the remaining positions.  Returns
+// false when every listed position was tested (alive is then exact over the
+// first 32 positions) or every window died.
 template <int K, bool kGlobal = false>
-__device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
+__device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
                                                     const uint4 *__restrict__ list,
                                                     uint32_t n_single, uint32_t n_general,
-                                                    const uint32_t (&valid)[G],
+                                                    uint32_t cut, const uint32_t (&valid)[G],
                                                     uint32_t (&alive)[G])
 {
     uint32_t L[G][K + 1];
@@ -195,7 +208,12 @@ __device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const u
         if (dead_all()) {
 #pragma unroll
             for (int g = 0; g < G; ++g) alive[g] = 0u;
-            return;
+            return false;
+        }
+        if (e + 4 >= cut) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
+            return true;
         }
     }
     for (; e < n_single; ++e) {
@@ -216,14 +234,22 @@ __device__ __forceinline__ void alive_window_sliced(const uint2 (&a)[G], const u
             const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, s);
             add(g, ~class_match(lo, hi, M));
         }
-        if ((c & 3) == 3 && dead_all()) {
+        if ((c & 3) == 3) {
+            if (dead_all()) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) alive[g] = 0u;
-            return;
+                for (int g = 0; g < G; ++g) alive[g] = 0u;
+                return false;
+            }
+            if (n_single + c + 1 >= cut) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
+                return true;
+            }
         }
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
+    return false;
 }
 
 // One warp tile and its halo, global -> shared, completing on bar.
@@ -315,6 +341,26 @@ __device__ __forceinline__ uint32_t settle_staged(uint32_t pass, uint64_t blk, u
     return pass;
 }
 
+// Exact counts of the windows still in `pass`, the first chunk from the
+// lane's blocks in registers (t0, t1), the rest through L1/L2 (any m):
+// drops those past k.
+__device__ __forceinline__ uint32_t settle_from_regs(uint32_t pass, uint64_t blk, uint2 t0, uint2 t1,
+                                                    const uint4 *__restrict__ M, uint32_t nchunks,
+                                                    uint32_t k, const uint2 *__restrict__ planes)
+{
+    if (!pass) return 0u;
+    const uint4 M0 = __ldg(M);
+    uint32_t sv = pass;
+    while (sv) {
+        const uint32_t w = __ffs(sv) - 1;
+        sv &= sv - 1;
+        uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), M0));
+        if (c <= k && nchunks > 1) c = window_count_from(planes, blk, w, M, 1, nchunks, c, k);
+        if (c > k) pass &= ~(1u << w);
+    }
+    return pass;
+}
+
 // Run-time constants of the pattern-sliced byte test for one k (k <= 63;
 // the kernels use it only where k < 32C).
 struct PsConst {
@@ -346,7 +392,14 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
 {
     const uint32_t k = (uint32_t)d.k;
     if constexpr (VARIANT >= 0) {
-        alive_window_sliced<VARIANT>(a, b, list, d.n_single, d.n_general, valid, pass);
+        const bool cut = alive_window_sliced<VARIANT>(a, b, list, d.n_single, d.n_general, ws_cut(VARIANT),
+                                                      valid, pass);
+        if (cut || d.nchunks > 1) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                pass[g] = settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, k, planes);
+        }
+        return;
     } else if constexpr (VARIANT == -2) {
         // k > 31: one chunk cannot decide; count all chunks (exact, nothing to settle)
 #pragma unroll 1
