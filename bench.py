@@ -52,7 +52,7 @@ VARIANT_NAMES = {1: "pattern-sliced", 2: "window-sliced", 3: "pattern-sliced-64"
 # profiles/k_scan_ncu_full_800M.md; scaled by the window count of a launch.
 # Valid for that kernel as captured: set it to None when the kernel changes.
 TRAFFIC_KERNEL = "k_scan<pattern-sliced>"
-TRAFFIC_BYTES_8E8 = (200.058880 + 4.104192) * 1e6
+TRAFFIC_BYTES_8E8 = (200.247808 + 4.095744) * 1e6
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, k = 16 m = 128 launch at "
                   "n = 8e8 (profiles/k_scan_ncu_full_800M.md), scaled by windows")
 
@@ -603,6 +603,9 @@ def run_serving(a):
     text = pm.pm_encode_text(host)
     qs = workloads.serving_queries(rate=a.rate, duration=a.duration)
     queries = [(q.arrival, q.pattern, q.k) for q in qs]
+    # the evaluation each k of the mix runs: measured on this GPU (or cached)
+    from paper_1611_06115_gb300 import tune
+    tv = tune.tune_variants(text, kmax=max(q.k for q in qs) + 1)
     backend = serve.GpuBackend(text, slots=4, batch={} if a.serve_mode == "one-launch" else None)
     # warm the kernels and the pool
     srv = serve.Server(backend, n=n, slots=4, max_batch=32, mem_budget=32 << 30)
@@ -615,6 +618,7 @@ def run_serving(a):
     ck = clocks.stop()
     n_cells = sum((n - len(r.pattern) + 1) * len(r.pattern) for r in srv.done)
     stats.update({"workload": "SERVING", "mode": a.serve_mode, "n": n, "offered_rate_qps": a.rate,
+                  "variant_per_k": {str(k): VARIANT_NAMES[v] for k, v in enumerate(tv["table"])},
                   "arrival_seconds": a.duration, "queries": len(queries),
                   "window_cells_per_s": n_cells / stats["span_s"],
                   "hits": int(sum(max(r.count, 0) for r in srv.done)), "clocks": ck,

@@ -189,7 +189,7 @@ Variant default_variant(int32_t k)
     // window-sliced counter wins while few positions decide a window, one
     // pattern-sliced chunk while the windows that survive it are rare, two
     // chunks while those surviving 64 positions are rare
-    if (k <= 4) return Variant::kWindowSliced;
+    if (k <= 5) return Variant::kWindowSliced;
     if (k <= 17) return Variant::kPatternSliced;
     if (k <= 40) return Variant::kPatternSliced2;
     return Variant::kAllChunks;
