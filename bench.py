@@ -584,7 +584,8 @@ def run_batched(a):
         "launch": "one persistent launch + ordering, replayed from a CUDA graph",
         "batch_options": tb["options"], "default_options_seconds": t_default,
         "tuning": {"seconds": tune_s, "variants_cached": tv["cached"], "batch_cached": tb["cached"],
-                   "batch_key": tb["key"], "candidates_timed": len(tb["log"])},
+                   "batch_key": tb["key"], "candidates_timed": len(tb["log"]),
+                   "whole_batch_check": tb.get("checked")},
     }), flush=True)
 
 

@@ -238,14 +238,20 @@ def sample_batch(patterns, k, size: int, seed: int = 0):
 
 
 def tune_batch(text, patterns, k, capacity: int, sample: int = 512, reps: int = 2,
-               cache: str | None = None, retune: bool = False, timer: Callable | None = None) -> dict:
+               cache: str | None = None, retune: bool = False, timer: Callable | None = None,
+               full_timer: Callable | None = None) -> dict:
     """Options for a pm_batch_create of these pairs: cached, else found by
     coordinate descent over BATCH_SPACE, each candidate timed as one
-    batched launch over a stratified sample of at most `sample` pairs.
+    batched launch over a stratified sample of at most `sample` pairs.  A
+    sample can favour options that do not carry over to the whole batch, so
+    the winner is then timed on the whole batch against the defaults and the
+    faster of the two is kept.
 
     patterns: compiled Pattern objects (or, with a timer, anything with an m).
-    timer: None to measure on the GPU, else timer(options) -> ms.
-    Returns {"key", "options", "ms", "cached", "log"}.
+    timer: None to measure on the GPU, else timer(options) -> ms on the
+    sample; full_timer likewise on the whole batch (None with a timer: no
+    check against the defaults).
+    Returns {"key", "options", "ms", "cached", "log", "checked"}.
     """
     ks = [int(x) for x in (k if not np.isscalar(k) else [k] * len(patterns))]
     ms = [p.m if hasattr(p, "m") else len(p) for p in patterns]
@@ -255,7 +261,8 @@ def tune_batch(text, patterns, k, capacity: int, sample: int = 512, reps: int = 
     data = load_cache(cache)
     entry = data.get(key)
     if entry and not retune:
-        return {"key": key, "options": entry["options"], "ms": entry.get("ms"), "cached": True, "log": []}
+        return {"key": key, "options": entry["options"], "ms": entry.get("ms"), "cached": True, "log": [],
+                "checked": entry.get("checked")}
     space = list(BATCH_SPACE)
     if timer is None:
         import torch
@@ -268,8 +275,8 @@ def tune_batch(text, patterns, k, capacity: int, sample: int = 512, reps: int = 
         space[-1] = ("grid", (0, sms, 2 * sms))
         st = torch.cuda.Stream()
 
-        def timer(o):  # noqa: F811 - the GPU timer
-            b = api.Batch(text, sp, sk, capacity=cap, stream=st, **o)
+        def gpu_time(pats, kk, cp, o):
+            b = api.Batch(text, pats, kk, capacity=cp, stream=st, **o)
             out = b.buffers()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             best = float("inf")
@@ -283,7 +290,20 @@ def tune_batch(text, patterns, k, capacity: int, sample: int = 512, reps: int = 
                         best = min(best, e0.elapsed_time(e1))
             b.free()
             return best
+
+        def timer(o):  # noqa: F811 - the GPU timer on the sample
+            return gpu_time(sp, sk, cap, o)
+
+        if full_timer is None:
+            def full_timer(o):  # on the whole batch
+                return gpu_time(patterns, ks, capacity, o)
     opts, t, log = coordinate_descent(timer, space)
-    data[key] = {"options": opts, "ms": t}
+    checked = None
+    if full_timer is not None and opts != BATCH_DEFAULTS:
+        t_best, t_def = float(full_timer(opts)), float(full_timer(dict(BATCH_DEFAULTS)))
+        checked = {"tuned_ms": t_best, "default_ms": t_def}
+        if t_def <= t_best:
+            opts, t = dict(BATCH_DEFAULTS), t_def
+    data[key] = {"options": opts, "ms": t, "checked": checked}
     save_cache(data, cache)
-    return {"key": key, "options": opts, "ms": t, "cached": False, "log": log}
+    return {"key": key, "options": opts, "ms": t, "cached": False, "log": log, "checked": checked}

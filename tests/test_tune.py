@@ -117,3 +117,23 @@ def test_probe_pattern_class_fraction():
     p = tune.probe_pattern(1000, rng)
     assert len(p) == 1000
     assert sum(c not in "ACGT" for c in p) == 100
+
+
+def test_tune_batch_keeps_defaults_when_the_whole_batch_disagrees(tmp_path):
+    """A sample can favour options that lose on the whole batch: the winner is
+    timed on the whole batch against the defaults and the faster is kept."""
+    class P:
+        def __init__(self, m):
+            self.m = m
+    pats = [P(100)] * 50
+    ks = [3] * 50
+    sample_timer = lambda o: 1.0 - 0.1 * (o["tiles"] == 4)
+    full_lose = lambda o: 2.0 if o["tiles"] == 4 else 1.5
+    r = tune.tune_batch(FakeText(), pats, ks, 100, cache=str(tmp_path / "a.json"), timer=sample_timer,
+                        full_timer=full_lose)
+    assert r["options"] == tune.BATCH_DEFAULTS and r["checked"]["default_ms"] == 1.5
+    full_win = lambda o: 1.0 if o["tiles"] == 4 else 1.5
+    r = tune.tune_batch(FakeText(), pats, ks, 100, cache=str(tmp_path / "b.json"), timer=sample_timer,
+                        full_timer=full_win)
+    assert r["options"]["tiles"] == 4 and r["checked"]["tuned_ms"] == 1.0
+
