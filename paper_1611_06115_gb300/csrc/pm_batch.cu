@@ -1,29 +1,32 @@
 // Batched search: many patterns of uneven m and k in one persistent launch
 // over the resident text.
 //
-// pm_batch_create sorts the (pattern, k) pairs into groups of up to kP pairs
-// of one kind: groups whose k is small (window-sliced evaluation, see
-// pm_scan.cu) and groups evaluated pattern-sliced.  Work items are (text
-// tile, group), tile-major, so that the warps running at any moment share a
-// few tiles in L2 and the text is read from device memory about once for
-// the whole batch.  A warp takes an item and stages the tile (plus halo) in
-// shared memory with one bulk copy, then
-//   * pattern-sliced group: for each window, the two funnel shifts that line
-//     the text up with positions 0..31 are done once and serve every pattern
-//     of the group (whose chunk-0 masks sit in shared memory), so a
-//     pattern-window costs three selects, one popcount and a quarter of the
-//     byte-packed threshold test;
-//   * window-sliced group: each pattern runs the thermometer-counter scan
-//     over the tile, reading its position list through the read-only path.
-// Every 1024-window group of a tile with hits for a pattern writes them
+// The planner sorts the (pattern, k) pairs into categories by evaluation
+// (window-sliced per k, pattern-sliced over 32 positions, over 64 positions,
+// every chunk; thresholds are options), orders each category by m and cuts
+// it into groups of kP pairs and rows of groups.  A work item is a row
+// crossed with a run of warp tiles; rows are outermost, so all warps run one
+// kind of evaluation at a time and the text is read from device memory
+// about once per row.  A warp stages its tiles (plus halo) in shared memory
+// by bulk copies two tiles ahead, then per group of the row
+//   * pattern-sliced group: for each window, the funnel shifts that line the
+//     text up with the first 32 (or 64) positions are done once and serve
+//     every pair of the group (whose masks sit in shared memory), so a
+//     pair-window costs three (or six) selects, one (or two) popcounts and a
+//     quarter of the byte-packed threshold test;
+//   * window-sliced group: each pair runs the thermometer-counter scan over
+//     the tile, reading its position list through the read-only path;
+//   * every-chunk group: each pair keeps 32 running counts per lane.
+// Every 1024-window group of a tile with hits for a pair writes them
 // contiguously, in window order, through a warp-aggregated atomic and
-// appends one segment record; records are radix-sorted by (pattern, tile,
+// appends one segment record; records are radix-sorted by (pair, tile,
 // group) (pm_sort.cu) and the ordering pass (pm_order.cu) lays the hits out
-// as per-pattern CSR lists sorted by location.
+// as per-pair CSR lists sorted by location.
 //
 // pm_batch_create allocates everything once; pm_batch_run allocates nothing
 // and never waits on the host, so it can be captured in a CUDA graph and
-// replayed.
+// replayed.  pm_search_ex with batch options runs the same plan with
+// stream-ordered scratch.
 #include <algorithm>
 #include <cstring>
 #include <new>

@@ -11,28 +11,36 @@
 // wait for each other: each persistent warp walks its own tiles, and a
 // tile's hits are emitted by a warp-aggregated atomic.
 //
-// The first 32 positions are evaluated in one of two ways.
+// Four evaluations, all exact, chosen per k (a measured table per device):
 //
-//  * pattern-sliced (any k): per window, one 32-bit word holds the text
-//    symbols under positions 0..31 (two funnel shifts of the bit planes);
-//    three bitwise selects apply Table 3 to all 32 pairs; __popc counts the
-//    matches g.  Four windows' g are packed into the bytes of one word by
-//    multiply-adds (FMA pipe) together with k in every byte; bit 5 of a byte
-//    is then set exactly when g + k >= 32, i.e. when the window has at most
-//    k mismatches, and two ALU steps move those four bits into the lane's
-//    pass mask (in a transposed bit order, undone only when a window passes).
+//  * pattern-sliced over 32 positions (k <= 31): per window, one 32-bit word
+//    holds the text symbols under positions 0..31 (two funnel shifts of the
+//    bit planes); three bitwise selects apply Table 3 to all 32 pairs;
+//    __popc counts the matches g.  Four windows' g are packed into the bytes
+//    of one word by multiply-adds (FMA pipe) together with k in every byte;
+//    bit 5 of a byte is then set exactly when g + k >= 32, i.e. when the
+//    window has at most k mismatches, and two ALU steps move those four bits
+//    into the lane's pass mask (in a transposed bit order, undone only when
+//    a window passes).  Windows that pass with m > 32 are settled: counted
+//    one at a time, the first two chunks from the still-staged tile, until
+//    their sum exceeds k or the pattern ends.
+//  * pattern-sliced over 64 positions (k <= 63): the same byte test over two
+//    chunks (bit 6), then the same settling.
+//  * every chunk (any k): 32 running counts per lane, chunk after chunk,
+//    until every window of the warp is past k.
 //  * window-sliced (k <= 6): per pattern position j, one word holds the 32
 //    windows' symbols at offset j; a one-letter class gives the mismatch word
 //    in two XOR/OR steps, other classes in three selects, N in none; a
 //    thermometer counter of k+1 words (level i set once a window has more
 //    than i mismatches) adds 32 windows' mismatches at once.  The positions
-//    come from a list built by pm_compile_pattern; each list entry read
-//    from shared memory serves all groups, and the warp stops as soon as
-//    every window of the tile is past k (the early stop of Sec. 2.4).
+//    come from a list built by pm_compile_pattern and ordered for the text
+//    (rarest letters first); each list entry read from shared memory serves
+//    all groups; the warp stops as soon as every window of the tile is past
+//    k (the early stop of Sec. 2.4), or after ws_cut(k) entries, where the
+//    few windows left are counted exactly one by one.
 //
-// Windows still at or below k after those 32 positions are counted again one
-// at a time, 32 positions per step, from position 0 until their sum exceeds k
-// or the pattern ends; that count is exact and is what a hit reports.
+// A hit's count is always exact (recounted over every position when the
+// evaluation stopped early for it).
 #include <cstring>
 #include <mutex>
 
