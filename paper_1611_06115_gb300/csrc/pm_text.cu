@@ -96,6 +96,12 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t n, uint64_t firs
                 }
             }
         }
+        // Unknown symbols read as A C G T A C G T ... by position in the
+        // planes: a pattern rarely matches that periodic text, so the exact
+        // recount of candidates (which gives them their true count) stays
+        // rare even inside long N runs.
+        lo = (lo & ~ub) | (0xaaaaaaaau & ub);
+        hi = (hi & ~ub) | (0xccccccccu & ub);
         planes[first / 32 + b] = make_uint2(lo, hi);
         if (unk) unk[first / 32 + b] = ub;
         nc += __popc(lo & ~hi & ~ub);
