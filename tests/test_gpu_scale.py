@@ -75,3 +75,49 @@ def test_full_size_unreported_windows_exceed_k(genome_run):
         cand = rng.integers(0, N - m + 1, size=25000, dtype=np.uint64)
         cand = np.setdiff1d(cand, loc.astype(np.uint64))[:20000]
         assert (oracle.counts_at(text, p, cand) > k).all()
+
+
+# ---- LARGE at full size: n = 3.1e9, m in {1e4, 1e5}, k in {0, 100, 1000} ----
+
+@pytest.fixture(scope="module")
+def large_run():
+    import torch
+    import paper_1611_06115_gb300 as pm
+    from synth import workloads
+
+    host = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    w = workloads.large(n=N, out=host.numpy())
+    t = pm.pm_encode_text(host)
+    res = {}
+    for p in w.patterns:
+        c = pm.pm_compile_pattern(p)
+        r = pm.pm_search(t, [c] * 3, list(w.meta["ks"]))
+        res[p] = [r.pattern(i) for i in range(3)]
+    del t
+    return host.numpy(), w, res
+
+
+def test_large_full_size_planted_reported_and_sampled(large_run):
+    """Every planted copy with s <= k is reported with its count; every
+    reported count is the oracle's; 2000 random unreported windows exceed k;
+    a slice of 2e5 windows matches the oracle window for window (k = 0, 100)."""
+    text, w, res = large_run
+    rng = np.random.default_rng(78)
+    for p, pl in zip(w.patterns, w.planted):
+        m = len(p)
+        for k, (loc, mm) in zip(w.meta["ks"], res[p]):
+            found = dict(zip(loc.tolist(), mm.tolist()))
+            for l, s in pl:
+                if s <= k:
+                    assert found.get(l) == s, (m, k, l, s)
+            assert (mm <= k).all()
+            if loc.size:
+                assert np.array_equal(oracle.counts_at(text, p, loc.astype(np.uint64)), mm)
+            cand = rng.integers(0, N - m + 1, size=2100, dtype=np.uint64)
+            cand = np.setdiff1d(cand, loc.astype(np.uint64))[:2000]
+            assert (oracle.counts_at(text, p, cand) > k).all()
+            if k <= 100:
+                a = int(rng.integers(0, N - m + 1 - 200_000))
+                el, em = oracle.search(text[a:a + 200_000 + m - 1], p, k)
+                sel = (loc >= a) & (loc < a + 200_000)
+                assert np.array_equal(loc[sel] - a, el) and np.array_equal(mm[sel], em), (m, k, a)
