@@ -160,12 +160,22 @@ __global__ void __launch_bounds__(kOrdThreads)
     const uint64_t entries = entry_count(n_max, n_dev);
     const uint64_t warps = (uint64_t)gridDim.x * (kOrdThreads / 32);
     const int lane = threadIdx.x & 31;
-    for (uint64_t e = (uint64_t)blockIdx.x * (kOrdThreads / 32) + (threadIdx.x >> 5); e < entries;
-         e += warps) {
-        const TileEntry te = table[e];
-        if (te.count == 0) continue;
-        const unsigned long long d = dest[e];
-        for (uint32_t i = lane; i < te.count; i += 32) hits[d + i] = tmp[(uint64_t)te.src + i];
+    // each lane reads one entry of a run of 32 (most entries are empty); the
+    // warp then copies the non-empty ones one after another, coalesced
+    for (uint64_t base = ((uint64_t)blockIdx.x * (kOrdThreads / 32) + (threadIdx.x >> 5)) * 32;
+         base < entries; base += warps * 32) {
+        const uint64_t e = base + (uint64_t)lane;
+        const TileEntry te = e < entries ? table[e] : TileEntry{0u, 0u};
+        const unsigned long long d = te.count ? dest[e] : 0ull;
+        uint32_t nz = __ballot_sync(0xffffffffu, te.count != 0u);
+        while (nz) {
+            const int j = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t cnt = __shfl_sync(0xffffffffu, te.count, j);
+            const uint64_t src = __shfl_sync(0xffffffffu, te.src, j);
+            const unsigned long long dd = __shfl_sync(0xffffffffu, d, j);
+            for (uint32_t i = lane; i < cnt; i += 32) hits[dd + i] = tmp[src + i];
+        }
     }
 }
 
@@ -189,7 +199,7 @@ void launch_gather(const TileEntry *table, uint64_t n_max, const unsigned long l
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t want = (n_max + (kOrdThreads / 32) - 1) / (kOrdThreads / 32);
+    const uint64_t want = (n_max + kOrdThreads - 1) / kOrdThreads;  // one run of 32 entries per warp
     uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
     if (grid < 1) grid = 1;
     k_gather<<<(unsigned)grid, kOrdThreads, 0, stream>>>(table, n_max, n_dev, dest, total, status,
