@@ -208,16 +208,24 @@ class Server:
 
 def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
     """Replay a list of (arrival seconds, pattern, k) on the server's clock in
-    real time, then drain.  Returns throughput and latency percentiles."""
+    real time, then drain.  Returns throughput, latency percentiles and the
+    queue depth (queries waiting for a slot), time-weighted over the arrival
+    period and at its peak."""
     queries = sorted(queries, key=lambda q: q[0])
     i = 0
     t_start = server.now()
+    t_prev, depth_area, depth_max = 0.0, 0.0, 0
+    t_arrivals_end = queries[-1][0] if queries else 0.0
     while i < len(queries) or not server.idle():
         now = server.now() - t_start
         while i < len(queries) and queries[i][0] <= now:
             a, p, k = queries[i]
             server.submit(p, k, arrival=t_start + a)
             i += 1
+        if now <= t_arrivals_end:
+            depth_area += len(server.queue) * (now - t_prev)
+            depth_max = max(depth_max, len(server.queue))
+            t_prev = now
         if server.step() == 0 and poll:
             time.sleep(poll)
     t_end = server.now()
@@ -233,6 +241,8 @@ def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
         "batches": server.batches,
         "max_concurrent_batches": server.max_inflight,
         "retries": sum(r.retries for r in server.done),
+        "queue_depth_mean": depth_area / t_prev if t_prev > 0 else 0.0,
+        "queue_depth_max": depth_max,
     }
 
 

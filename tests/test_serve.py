@@ -136,3 +136,14 @@ def test_overflow_reruns_with_exact_count():
     srv.drain()
     el, _ = oracle.search(text, "ACG", 1)
     assert r.retries == 1 and r.count == el.size and np.array_equal(r.hits[0], el)
+
+
+def test_queue_depth_reported_and_grows_under_overload():
+    text = synth.markov_text(100_000, seed=23)
+    rng = np.random.default_rng(23)
+    slow = FakeBackend(text, delay=0.05)
+    srv = serve.Server(slow, n=text.size, slots=1, max_batch=1, mem_budget=1 << 40)
+    qs = [(0.002 * i, synth.random_pattern(12, 1, rng), 1) for i in range(40)]
+    st = serve.run_trace(srv, qs)
+    assert st["completed"] == 40
+    assert st["queue_depth_max"] >= 10 and st["queue_depth_mean"] > 1.0
