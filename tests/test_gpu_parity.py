@@ -101,22 +101,29 @@ def test_planted_copies_many_tiles_ragged(pm):
                 assert found.get(loc) == s
 
 
-def test_dense_hits_every_window(pm):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_dense_hits_every_window(pm, variant):
     n = 3 * 8192 + 4321
     text = synth.uniform_text(n, seed=3)
     for m, k in ((1, 1), (40, 40), (70, 100)):
         pat = ("MRWSYKVHDB" * 10)[:m]
-        l, c = gpu_hits(pm, text, [pat], [k])[0]
+        l, c = gpu_hits(pm, text, [pat], [k], variant=variant)[0]
         assert l.tolist() == list(range(n - m + 1))
         assert np.array_equal(c, oracle.counts(text, pat))
 
 
-def test_edges_m_vs_n(pm):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_edges_m_vs_n(pm, variant):
     text = synth.uniform_text(100, seed=4)
-    (l, _), = gpu_hits(pm, text, ["A" * 101], [200])
+    (l, _), = gpu_hits(pm, text, ["A" * 101], [200], variant=variant)
     assert l.size == 0
-    (l, c), = gpu_hits(pm, text, [bytes(text).decode()], [0])
+    (l, c), = gpu_hits(pm, text, [bytes(text).decode()], [0], variant=variant)
     assert l.tolist() == [0] and c.tolist() == [0]
+    for k in (0, 3, 6):  # one window per tile edge region: n = 4096*32*j + r
+        t2 = synth.uniform_text(4096 * 32 + 33, seed=40 + k)
+        pat = bytes(t2[4096 * 32 - 5:4096 * 32 + 27]).decode()  # straddles the first tile boundary
+        (l, c), = gpu_hits(pm, t2, [pat], [k], variant=variant)
+        same((l, c), oracle.search(t2, pat, k))
     t0 = pm.pm_encode_text(b"")
     r = pm.pm_search(t0, [pm.pm_compile_pattern("ACG")], [1])
     assert r.total == 0 and r.offsets.cpu().tolist() == [0, 0]
