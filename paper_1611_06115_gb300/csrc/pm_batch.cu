@@ -314,90 +314,108 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
             }
             return;
         }
-        // the tile stays staged until the item is done: evaluations read
-        // their blocks from it when they need them
         const uint2 *stage = &sbuf[warp][st][0];
         const uint2 ph = __ldg(ba.phases + cp.row);
-        for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
-            const uint32_t pfirst = grp * kP;
-            const uint32_t gk = __ldg(ba.gkind + grp);
-            const uint32_t kind = gk & 3u, cnt = gk >> 2;
-
-            if (kind == kKindLong) {
-                // ---- every chunk counted, one pattern at a time ----
-                for (uint32_t i = 0; i < cnt; ++i) {
-                    const uint32_t p = __ldg(ba.order + pfirst + i);
-                    const PatDesc d = ba.pats[p];
-                    const uint4 *M = ba.arena + d.masks;
-#pragma unroll 1
-                    for (int g = 0; g < G; ++g) {
-                        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                        const uint32_t valid = valid_mask(blk, d.nwin);
-                        const uint32_t pass = pass_multi_chunk(ba.planes, blk, M, d.nchunks, (uint32_t)d.k,
-                                                               valid, stage[32 * g + lane],
-                                                               stage[32 * g + lane + 1]);
-                        if (__any_sync(kFull, pass != 0u))
-                            emit_group(pass, blk, p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                       d.nchunks, (uint32_t)d.k, M, ba);
-                    }
-                }
-            } else if (kind == kKindShort) {
-                if (cnt == kP) short_group<1, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-                else short_group<1, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-            } else if (kind == kKindShort2) {
-                if (cnt == kP) short_group<2, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-                else short_group<2, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-            } else {
-                // ---- window-sliced group: one pattern at a time over all groups ----
-                for (uint32_t i = 0; i < cnt; ++i) {
-                    const uint32_t p = __ldg(ba.order + pfirst + i);
-                    const PatDesc d = ba.pats[p];
-                    uint64_t blk[G];
-                    uint32_t valid[G], pass[G];
-                    uint2 a[G], b[G];
-                    uint32_t anyv = 0;
+        const uint32_t kind0 = __ldg(ba.gkind + ph.x) & 3u;  // a row holds one kind
+        if (kind0 == kKindWs) {
+            // The window-sliced evaluation needs only the lane's two blocks per
+            // group: take them into registers and refill the stage now, two
+            // tiles ahead (its items are short; a refill after the item would
+            // leave the next copy too little time to land).
+            uint2 a[G], b[G];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        a[g] = stage[32 * g + lane];
-                        b[g] = stage[32 * g + lane + 1];
-                        blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                        valid[g] = valid_mask(blk[g], d.nwin);
-                        anyv |= valid[g];
-                    }
-                    if (!__any_sync(kFull, anyv != 0u)) continue;
-                    const uint4 *list = ba.arena + d.wslist;
-                    bool cut;
-                    // only the thresholds this batch uses are compiled in (instruction cache)
-                    if (d.k == 0) cut = alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, ws_cut(0), valid, pass);
-                    else if (WSMAX >= 1 && d.k == 1) cut = alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 1 ? 1 : 0)), valid, pass);
-                    else if (WSMAX >= 2 && d.k == 2) cut = alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 2 ? 2 : 0)), valid, pass);
-                    else if (WSMAX >= 3 && d.k == 3) cut = alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 3 ? 3 : 0)), valid, pass);
-                    else if (WSMAX >= 4 && d.k == 4) cut = alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 4 ? 4 : 0)), valid, pass);
-                    else if (WSMAX >= 5 && d.k == 5) cut = alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 5 ? 5 : 0)), valid, pass);
-                    else cut = alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 6 ? 6 : 0)), valid, pass);
-                    const uint4 *M = ba.arena + d.masks;
+            for (int g = 0; g < G; ++g) {
+                a[g] = stage[32 * g + lane];
+                b[g] = stage[32 * g + lane + 1];
+            }
+            __syncwarp();
+            if (lane == 0 && pp.row < nrows) {
+                dev::fence_proxy_async_smem();
+                issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
+            }
+            advance(pp);
+            for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
+                const uint32_t pfirst = grp * kP;
+                const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
+                {
+                    // ---- window-sliced group: one pattern at a time over all groups ----
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const uint32_t p = __ldg(ba.order + pfirst + i);
+                        const PatDesc d = ba.pats[p];
+                        uint64_t blk[G];
+                        uint32_t valid[G], pass[G];
+                        uint32_t anyv = 0;
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const uint32_t ps = d.nchunks > 1
-                            ? settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M,
-                                            d.nchunks, (uint32_t)d.k, ba.planes)
-                            : cut ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, (uint32_t)d.k,
-                                                     ba.planes)
-                                  : pass[g];
-                        if (__any_sync(kFull, ps != 0u))
-                            emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                       d.nchunks, (uint32_t)d.k, M, ba);
+                        for (int g = 0; g < G; ++g) {
+                            blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+                            valid[g] = valid_mask(blk[g], d.nwin);
+                            anyv |= valid[g];
+                        }
+                        if (!__any_sync(kFull, anyv != 0u)) continue;
+                        const uint4 *list = ba.arena + d.wslist;
+                        bool cut;
+                        // only the thresholds this batch uses are compiled in (instruction cache)
+                        if (d.k == 0) cut = alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, ws_cut(0), valid, pass);
+                        else if (WSMAX >= 1 && d.k == 1) cut = alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 1 ? 1 : 0)), valid, pass);
+                        else if (WSMAX >= 2 && d.k == 2) cut = alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 2 ? 2 : 0)), valid, pass);
+                        else if (WSMAX >= 3 && d.k == 3) cut = alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 3 ? 3 : 0)), valid, pass);
+                        else if (WSMAX >= 4 && d.k == 4) cut = alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 4 ? 4 : 0)), valid, pass);
+                        else if (WSMAX >= 5 && d.k == 5) cut = alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 5 ? 5 : 0)), valid, pass);
+                        else cut = alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 6 ? 6 : 0)), valid, pass);
+                        const uint4 *M = ba.arena + d.masks;
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            const uint32_t ps = (cut || d.nchunks > 1)
+                                ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, (uint32_t)d.k,
+                                                   ba.planes)
+                                : pass[g];
+                            if (__any_sync(kFull, ps != 0u))
+                                emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
+                                           d.nchunks, (uint32_t)d.k, M, ba);
+                        }
                     }
                 }
             }
-        }  // groups of the item
-        // the tile is done: refill its stage with sequence position s + 2
-        __syncwarp();
-        if (lane == 0 && pp.row < nrows) {
-            dev::fence_proxy_async_smem();
-            issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
+        } else {
+            // pattern-sliced groups read the staged tile while they settle the
+            // windows that survive their first chunks (and the every-chunk
+            // groups read it per group): refill after the item
+            for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
+                const uint32_t pfirst = grp * kP;
+                const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
+                if (kind0 == kKindLong) {
+                    // ---- every chunk counted, one pattern at a time ----
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const uint32_t p = __ldg(ba.order + pfirst + i);
+                        const PatDesc d = ba.pats[p];
+                        const uint4 *M = ba.arena + d.masks;
+#pragma unroll 1
+                        for (int g = 0; g < G; ++g) {
+                            const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+                            const uint32_t valid = valid_mask(blk, d.nwin);
+                            const uint32_t pass = pass_multi_chunk(ba.planes, blk, M, d.nchunks, (uint32_t)d.k,
+                                                                   valid, stage[32 * g + lane],
+                                                                   stage[32 * g + lane + 1]);
+                            if (__any_sync(kFull, pass != 0u))
+                                emit_group(pass, blk, p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
+                                           d.nchunks, (uint32_t)d.k, M, ba);
+                        }
+                    }
+                } else if (kind0 == kKindShort) {
+                    if (cnt == kP) short_group<1, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                    else short_group<1, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                } else {
+                    if (cnt == kP) short_group<2, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                    else short_group<2, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && pp.row < nrows) {
+                dev::fence_proxy_async_smem();
+                issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
+            }
+            advance(pp);
         }
-        advance(pp);
     }
 }
 
