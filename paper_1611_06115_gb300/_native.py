@@ -68,6 +68,8 @@ SIGNATURES = {
     "pm_text_free": (None, [_vp]),
     "pm_encode_text_ex": (_i32, [_vp, _u64, _u32, _vp, ctypes.POINTER(_vp)]),
     "pm_text_unknown": (_u64, [_vp]),
+    "pm_text_save": (_i32, [_vp, ctypes.c_char_p]),
+    "pm_text_load": (_i32, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
     "pm_text_letter_counts": (_i32, [_vp, ctypes.POINTER(_u64)]),
     "pm_compile_pattern": (_i32, [ctypes.c_char_p, _u32, ctypes.POINTER(_vp)]),
     "pm_pattern_length": (_u32, [_vp]),

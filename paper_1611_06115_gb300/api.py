@@ -7,6 +7,7 @@ and streams.
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -55,6 +56,19 @@ class Text:
         N.check(N.lib().pm_text_device_planes(self._h, ctypes.byref(p), ctypes.byref(b)),
                 "pm_text_device_planes")
         return int(p.value or 0), int(b.value)
+
+    def save(self, path: str) -> None:
+        """Write the coded text to a file (pm_text_save)."""
+        N.check(N.lib().pm_text_save(self._h, os.fsencode(path)), "pm_text_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Text":
+        """Read a coded text written by save() onto the current device
+        (pm_text_load)."""
+        out = ctypes.c_void_p()
+        N.check(N.lib().pm_text_load(os.fsencode(path), _stream(stream), ctypes.byref(out)),
+                "pm_text_load")
+        return cls(out, int(N.lib().pm_text_length(out)))
 
     def unknown(self) -> int:
         """Symbols coded as unknown (pm_text_unknown)."""

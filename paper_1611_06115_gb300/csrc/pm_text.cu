@@ -14,6 +14,8 @@
 //              2^21 land on distinct positions and those of interest are
 //              21..24.
 #include <cstdarg>
+#include <vector>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -313,6 +315,158 @@ pm_status pm_text_device_planes(const pm_text *text, const void **planes, uint64
     if (!text) return PM_E_ARG;
     if (planes) *planes = text->planes;
     if (bytes) *bytes = text->nblocks * sizeof(uint2);
+    return PM_OK;
+}
+
+// ---- coded-text files ----
+//
+// Layout (little-endian u64 fields): magic "PMTEXT1\0", n, nblocks,
+// n_unknown, count[4], has_unknown_bits, checksum; then the planes (nblocks
+// x 8 bytes) and, when has_unknown_bits, the unknown bits (nblocks x 4
+// bytes).  The checksum is FNV-1a over 64-bit words (offset basis and prime
+// of the 64-bit FNV) of the header fields before it and of the data.
+
+namespace {
+constexpr char kMagic[8] = {'P', 'M', 'T', 'E', 'X', 'T', '1', '\0'};
+constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull, kFnvPrime = 0x100000001b3ull;
+
+uint64_t fnv_words(uint64_t h, const void *p, size_t bytes)
+{
+    const unsigned char *c = (const unsigned char *)p;
+    size_t i = 0;
+    for (; i + 8 <= bytes; i += 8) {
+        uint64_t w;
+        std::memcpy(&w, c + i, 8);
+        h = (h ^ w) * kFnvPrime;
+    }
+    for (; i < bytes; ++i) h = (h ^ c[i]) * kFnvPrime;
+    return h;
+}
+
+struct TextHeader {
+    char magic[8];
+    uint64_t n, nblocks, n_unknown, count[4], has_unk, checksum;
+};
+}  // namespace
+
+pm_status pm_text_save(const pm_text *text, const char *path)
+{
+    if (!text || !path) {
+        set_error("pm_text_save: NULL argument");
+        return PM_E_ARG;
+    }
+    TextHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.n = text->n;
+    h.nblocks = text->nblocks;
+    h.n_unknown = text->n_unknown;
+    for (int i = 0; i < 4; ++i) h.count[i] = text->count[i];
+    h.has_unk = text->unk ? 1u : 0u;
+    std::vector<uint2> planes;
+    std::vector<uint32_t> unk;
+    try {
+        planes.resize(text->nblocks);
+        if (text->unk) unk.resize(text->nblocks);
+    } catch (...) {
+        set_error("pm_text_save: no host memory for %llu blocks", (unsigned long long)text->nblocks);
+        return PM_E_NOMEM;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != text->device) cudaSetDevice(text->device);
+    pm_status rc = cuda_status(cudaMemcpy(planes.data(), text->planes, text->nblocks * sizeof(uint2),
+                                          cudaMemcpyDeviceToHost), "copy planes");
+    if (!rc && text->unk)
+        rc = cuda_status(cudaMemcpy(unk.data(), text->unk, text->nblocks * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost), "copy unknown bits");
+    if (cur != text->device) cudaSetDevice(cur);
+    if (rc) return rc;
+    uint64_t c = fnv_words(kFnvBasis, &h, offsetof(TextHeader, checksum));
+    c = fnv_words(c, planes.data(), planes.size() * sizeof(uint2));
+    if (text->unk) c = fnv_words(c, unk.data(), unk.size() * sizeof(uint32_t));
+    h.checksum = c;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) {
+        set_error("pm_text_save: cannot open %s", path);
+        return PM_E_ARG;
+    }
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+              std::fwrite(planes.data(), sizeof(uint2), planes.size(), f) == planes.size() &&
+              (!text->unk || std::fwrite(unk.data(), sizeof(uint32_t), unk.size(), f) == unk.size());
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("pm_text_save: write to %s failed", path);
+        return PM_E_ARG;
+    }
+    return PM_OK;
+}
+
+pm_status pm_text_load(const char *path, void *stream, pm_text **out)
+{
+    if (!path || !out) {
+        set_error("pm_text_load: NULL argument");
+        return PM_E_ARG;
+    }
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) {
+        set_error("pm_text_load: cannot open %s", path);
+        return PM_E_ARG;
+    }
+    TextHeader h{};
+    auto fail = [&](pm_status rc, const char *why) {
+        std::fclose(f);
+        set_error("pm_text_load: %s: %s", path, why);
+        return rc;
+    };
+    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0)
+        return fail(PM_E_ARG, "not a coded-text file");
+    if (h.n >= (1ull << 32) || h.nblocks != (h.n + 31) / 32 + kPadBlocks || h.has_unk > 1)
+        return fail(PM_E_ARG, "inconsistent header");
+    std::vector<uint2> planes;
+    std::vector<uint32_t> unk;
+    try {
+        planes.resize(h.nblocks);
+        if (h.has_unk) unk.resize(h.nblocks);
+    } catch (...) {
+        return fail(PM_E_NOMEM, "no host memory");
+    }
+    if (std::fread(planes.data(), sizeof(uint2), planes.size(), f) != planes.size() ||
+        (h.has_unk && std::fread(unk.data(), sizeof(uint32_t), unk.size(), f) != unk.size()))
+        return fail(PM_E_ARG, "file is short");
+    std::fclose(f);
+    uint64_t c = fnv_words(kFnvBasis, &h, offsetof(TextHeader, checksum));
+    c = fnv_words(c, planes.data(), planes.size() * sizeof(uint2));
+    if (h.has_unk) c = fnv_words(c, unk.data(), unk.size() * sizeof(uint32_t));
+    if (c != h.checksum) {
+        set_error("pm_text_load: %s: checksum mismatch", path);
+        return PM_E_ARG;
+    }
+    pm_text *t = new (std::nothrow) pm_text{};
+    if (!t) return PM_E_NOMEM;
+    cudaGetDevice(&t->device);
+    t->n = h.n;
+    t->nblocks = h.nblocks;
+    t->n_unknown = h.n_unknown;
+    for (int i = 0; i < 4; ++i) t->count[i] = h.count[i];
+    cudaStream_t st = (cudaStream_t)stream;
+    pm_status rc = cuda_status(cudaMalloc(&t->planes, t->nblocks * sizeof(uint2)), "cudaMalloc planes");
+    if (!rc && h.has_unk)
+        rc = cuda_status(cudaMalloc(&t->unk, t->nblocks * sizeof(uint32_t)), "cudaMalloc unknown bits");
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(t->planes, planes.data(), t->nblocks * sizeof(uint2),
+                                         cudaMemcpyHostToDevice, st), "upload planes");
+    if (!rc && h.has_unk)
+        rc = cuda_status(cudaMemcpyAsync(t->unk, unk.data(), t->nblocks * sizeof(uint32_t),
+                                         cudaMemcpyHostToDevice, st), "upload unknown bits");
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "stream synchronize");
+    if (rc) {
+        if (t->planes) cudaFree(t->planes);
+        if (t->unk) cudaFree(t->unk);
+        delete t;
+        return rc;
+    }
+    *out = t;
     return PM_OK;
 }
 

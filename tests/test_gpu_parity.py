@@ -336,3 +336,38 @@ def test_letter_counts_and_position_order(pm):
             got = gpu_hits(pm, text, pats, [k] * 3, variant=v)
             for p, g in zip(pats, got):
                 same(g, oracle.search(text, p, k))
+
+
+def test_text_save_and_load(pm, tmp_path):
+    """A coded text written to a file and read back searches the same; a
+    corrupted or foreign file is refused."""
+    rng = np.random.default_rng(91)
+    text = synth.markov_text(2 * 4096 * 32 + 71, seed=91)
+    unk = text.copy()
+    unk[5000:5400] = ord("N")
+    pats = [synth.random_pattern(m, m // 10, rng) for m in (20, 64, 300)]
+    for src, flags in ((text, 0), (unk, pm.PM_TEXT_UNKNOWN_AS_N)):
+        t = pm.pm_encode_text_ex(src, flags=flags)
+        path = str(tmp_path / f"t{flags}.pmtext")
+        t.save(path)
+        back = pm.Text.load(path)
+        assert back.n == t.n and back.unknown() == t.unknown()
+        assert back.letter_counts() == t.letter_counts()
+        cps = [pm.pm_compile_pattern(p) for p in pats]
+        a = pm.pm_search(t, cps, [0, 3, 12])
+        b = pm.pm_search(back, cps, [0, 3, 12])
+        assert np.array_equal(a.numpy()[0], b.numpy()[0]) and np.array_equal(a.numpy()[1], b.numpy()[1])
+        for i, (p, k) in enumerate(zip(pats, (0, 3, 12))):
+            exp = oracle.search_unknown_text(src, p, k) if flags else oracle.search(src, p, k)
+            same(b.pattern(i), exp)
+        raw = bytearray(open(path, "rb").read())
+        raw[-100] ^= 0x40
+        bad = str(tmp_path / "bad.pmtext")
+        open(bad, "wb").write(bytes(raw))
+        with pytest.raises(pm.PmError) as e:
+            pm.Text.load(bad)
+        assert e.value.status == pm.PM_E_ARG
+    foreign = str(tmp_path / "foreign")
+    open(foreign, "wb").write(b"ACGT" * 100)
+    with pytest.raises(pm.PmError):
+        pm.Text.load(foreign)
