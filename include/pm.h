@@ -375,6 +375,19 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
 /* ----------------------------------------------------------- measurement */
 
 /*
+ * pm_check_bounded_wait -- failure detection, checked without a fault.  The
+ * paper has no counterpart.  Every wait of the scan kernels on a bulk copy
+ * gives up after a time limit (1 s in the kernels), sets a status bit and
+ * returns, so a lost copy ends as PM_E_TIMEOUT instead of a hung GPU.  This
+ * entry point runs that same bounded wait once, in a one-warp kernel, on a
+ * barrier that receives its arrival only if `arrive` is nonzero, with the
+ * given limit (1 ns .. 10 s; PM_E_ARG otherwise), and reports through
+ * *timed_out whether the wait gave up (1) or completed (0).  Nothing is left
+ * pending on the device either way.
+ */
+pm_status pm_check_bounded_wait(uint64_t limit_ns, int32_t arrive, uint32_t *timed_out);
+
+/*
  * pm_measure_int_pipe -- throughput of one integer instruction kind on the
  * current device, for the ALU roofline of the scan kernels.  The paper has
  * no counterpart (its timings are of a CPU program).

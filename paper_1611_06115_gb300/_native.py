@@ -89,6 +89,7 @@ SIGNATURES = {
     "pm_batch_run": (_i32, [_vp, _vp, _vp, _vp]),
     "pm_batch_capacity": (_u64, [_vp]),
     "pm_batch_free": (None, [_vp]),
+    "pm_check_bounded_wait": (_i32, [_u64, _i32, ctypes.POINTER(_u32)]),
     "pm_measure_int_pipe": (_i32, [_i32, _u32, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pm_status_string": (ctypes.c_char_p, [_i32]),

@@ -361,6 +361,15 @@ def pm_get_auto_variants(nk: int = 64) -> list[int]:
     return list(arr)[:nk]
 
 
+def pm_check_bounded_wait(limit_ns: int, arrive: bool) -> bool:
+    """Run the kernels' bounded barrier wait once (include/pm.h); True when
+    it gave up after limit_ns."""
+    out = ctypes.c_uint32(0)
+    N.check(N.lib().pm_check_bounded_wait(int(limit_ns), 1 if arrive else 0, ctypes.byref(out)),
+            "pm_check_bounded_wait")
+    return bool(out.value)
+
+
 def pm_measure_int_pipe(op: int, iters: int = 20000) -> dict:
     """Measured throughput of one integer instruction kind (see include/pm.h)."""
     ops, mhz, per = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

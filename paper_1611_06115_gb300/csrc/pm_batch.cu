@@ -754,6 +754,7 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
                           const int32_t *k, uint64_t capacity, const pm_batch_options *opts,
                           void *stream, pm_batch **out)
 {
+    TraceRange trace("pm_batch_create");
     if (!text || !out || (npat > 0 && (!patterns || !k))) {
         set_error("pm_batch_create: NULL argument");
         return PM_E_ARG;
@@ -789,6 +790,7 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
 
 pm_status pm_batch_run(pm_batch *b, pm_hit *hits, uint64_t *offsets, void *stream)
 {
+    TraceRange trace("pm_batch_run");
     if (!b || !offsets || (b->capacity > 0 && !hits)) {
         set_error("pm_batch_run: NULL argument");
         return PM_E_ARG;

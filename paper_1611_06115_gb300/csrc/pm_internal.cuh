@@ -19,6 +19,8 @@
 
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pm.h"
 
 struct pm_text {
@@ -48,6 +50,15 @@ struct pm_pattern {
 };
 
 namespace pm {
+
+// A named range on the host timeline for profilers (NVTX; costs nothing when
+// no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // The window-sliced list of p (see pm_pattern) reordered for text t so that
 // windows die as early as possible (the early stop of Sec. 2.4 then ends the

@@ -61,7 +61,59 @@ __global__ void __launch_bounds__(256) k_intpipe(uint32_t *out, uint32_t iters, 
 
 using namespace pm;
 
+namespace pm {
+namespace {
+
+// The bounded barrier wait every scan kernel uses on its bulk copies, on a
+// barrier that receives its one arrival only if `arrive` is set: without it
+// nothing completes the phase and the wait must give up after limit_ns.
+// out[0] = 1 when the wait gave up, out[1] = 1 once the kernel returned.
+__global__ void k_bounded_wait(uint64_t limit_ns, int arrive, uint32_t *out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) dev::mbar_arrive_expect_tx(&bar, 0);
+        const bool ok = dev::mbar_wait_bounded(&bar, 0u, limit_ns);
+        out[0] = ok ? 0u : 1u;
+        out[1] = 1u;
+    }
+}
+
+}  // namespace
+}  // namespace pm
+
 extern "C" {
+
+pm_status pm_check_bounded_wait(uint64_t limit_ns, int32_t arrive, uint32_t *timed_out)
+{
+    if (!timed_out || limit_ns == 0 || limit_ns > 10000000000ull) {
+        set_error("pm_check_bounded_wait: NULL output or limit outside 1 ns .. 10 s");
+        return PM_E_ARG;
+    }
+    uint32_t *d = nullptr;
+    pm_status rc = cuda_status(cudaMalloc(&d, 2 * sizeof(uint32_t)), "cudaMalloc");
+    if (rc) return rc;
+    uint32_t h[2] = {0u, 0u};
+    rc = cuda_status(cudaMemset(d, 0, 2 * sizeof(uint32_t)), "cudaMemset");
+    if (!rc) {
+        k_bounded_wait<<<1, 32>>>(limit_ns, arrive ? 1 : 0, d);
+        rc = cuda_status(cudaGetLastError(), "launch");
+    }
+    if (!rc) rc = cuda_status(cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost), "copy result");
+    cudaFree(d);
+    if (rc) return rc;
+    if (h[1] != 1u) {
+        set_error("pm_check_bounded_wait: the kernel did not finish");
+        return PM_E_CUDA;
+    }
+    *timed_out = h[0];
+    return PM_OK;
+}
 
 pm_status pm_measure_int_pipe(int32_t op, uint32_t iters, double *ops_per_s, double *sm_mhz,
                               double *ops_per_clk_per_sm)

@@ -77,6 +77,7 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
                             const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
                             uint64_t *needed, void *stream)
 {
+    TraceRange trace("pm_search_noalloc");
     if (!text || !offsets || (npat > 0 && (!patterns || !k)) || (capacity > 0 && !hits)) {
         set_error("pm_search_noalloc: NULL argument");
         return PM_E_ARG;

@@ -153,6 +153,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
                        const int32_t *k, pm_hit *hits, uint64_t capacity, uint64_t *offsets,
                        uint64_t *needed, const pm_options *opts, void *stream)
 {
+    TraceRange trace("pm_search");
     if (!text || !offsets || (npat > 0 && (!patterns || !k)) || (capacity > 0 && !hits)) {
         set_error("pm_search: NULL argument");
         return PM_E_ARG;

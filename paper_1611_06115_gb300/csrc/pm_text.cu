@@ -213,6 +213,7 @@ pm_status pm_encode_text(const char *ascii, uint64_t n, void *stream, pm_text **
 
 pm_status pm_encode_text_ex(const char *ascii, uint64_t n, uint32_t flags, void *stream, pm_text **out)
 {
+    TraceRange trace("pm_encode_text");
     if (!out || (!ascii && n > 0) || (flags & ~PM_TEXT_UNKNOWN_AS_N)) {
         set_error("pm_encode_text: NULL argument or unknown flags 0x%x", flags);
         return PM_E_ARG;
@@ -403,6 +404,7 @@ pm_status pm_text_save(const pm_text *text, const char *path)
 
 pm_status pm_text_load(const char *path, void *stream, pm_text **out)
 {
+    TraceRange trace("pm_text_load");
     if (!path || !out) {
         set_error("pm_text_load: NULL argument");
         return PM_E_ARG;

@@ -1,0 +1,63 @@
+"""Failure detection without a GPU fault: the bounded barrier wait every
+scan kernel uses on its bulk copies gives up after its limit when nothing
+completes the barrier, the kernel returns, and the context stays usable;
+capacity overflows and bad arguments come back as status codes."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1611_06115_gb300 as pm
+    pm.lib()
+    return pm
+
+
+def test_wait_that_nothing_completes_times_out_and_returns(pm):
+    t0 = time.perf_counter()
+    assert pm.api.pm_check_bounded_wait(2_000_000, arrive=False) is True  # 2 ms limit
+    dt = time.perf_counter() - t0
+    assert dt < 5.0
+    assert pm.api.pm_check_bounded_wait(2_000_000, arrive=True) is False
+    with pytest.raises(pm.PmError) as e:
+        pm.api.pm_check_bounded_wait(0, arrive=False)
+    assert e.value.status == pm.PM_E_ARG
+    # the context is still usable: a search right after gives the oracle's hits
+    text = synth.markov_text(4096 * 32 + 9, seed=3)
+    t = pm.pm_encode_text(text)
+    r = pm.pm_search(t, [pm.pm_compile_pattern("ACGTRYACGT")], [2])
+    l, c = r.pattern(0)
+    el, ec = oracle.search(text, "ACGTRYACGT", 2)
+    assert np.array_equal(l, el) and np.array_equal(c, ec)
+
+
+def test_status_codes_instead_of_faults(pm):
+    import torch
+    text = synth.markov_text(50_000, seed=4)
+    t = pm.pm_encode_text(text)
+    p = pm.pm_compile_pattern("ACGTNNAC")
+    with pytest.raises(pm.PmError) as e:  # too small an output
+        pm.pm_search_ex(t, [p], [3], capacity=1, out="host")
+    assert e.value.status == pm.PM_E_OVERFLOW
+    with pytest.raises(pm.PmError) as e:  # unknown variant
+        pm.pm_search_ex(t, [p], [3], variant=9)
+    assert e.value.status == pm.PM_E_ARG
+    with pytest.raises(pm.PmError) as e:  # negative k
+        pm.pm_search(t, [p], [-1])
+    assert e.value.status == pm.PM_E_ARG
+    with pytest.raises(pm.PmError) as e:  # batch option out of range
+        pm.Batch(t, [p], [3], capacity=10, tiles=9)
+    assert e.value.status == pm.PM_E_ARG
+    with pytest.raises(pm.PmError) as e:  # a symbol outside Table 1
+        pm.pm_encode_text(b"ACGTX")
+    assert e.value.status == pm.PM_E_SYMBOL
+    torch.cuda.synchronize()
