@@ -99,6 +99,8 @@ class Request:
     hits: object = None             # backend-specific (locations, mismatches)
     count: int = -1
     retries: int = 0
+    deadline: float | None = None   # server clock; expires if not started by then
+    status: str = "queued"          # queued, running, done, cancelled, expired
 
     @property
     def latency(self) -> float:
@@ -128,6 +130,8 @@ class Server:
         self.free_slots = list(range(slots))
         self.flights: list[_Flight] = []
         self.done: list[Request] = []
+        self.cancelled: list[Request] = []
+        self.expired: list[Request] = []
         self.inflight_bytes = 0
         self._next = 0
         self.batches = 0
@@ -136,12 +140,44 @@ class Server:
     def now(self) -> float:
         return self.clock() - self.t0
 
-    def submit(self, pattern: str, k: int, arrival: float | None = None) -> Request:
+    def submit(self, pattern: str, k: int, arrival: float | None = None,
+               timeout: float | None = None) -> Request:
+        """Queue a query.  timeout: seconds after arrival by which it must
+        have started, else it expires unanswered."""
         r = Request(self._next, pattern, int(k), self.now() if arrival is None else arrival)
         r.capacity = capacity_for(pattern, k, self.n)
+        if timeout is not None:
+            r.deadline = r.arrival + timeout
         self._next += 1
         self.queue.append(r)
         return r
+
+    def cancel(self, r: Request) -> bool:
+        """Withdraw a query: a queued one never starts; a running one's
+        results are dropped when its batch finishes.  False if it already
+        finished (or was withdrawn)."""
+        if r.status == "queued":
+            self.queue.remove(r)
+            r.status = "cancelled"
+            self.cancelled.append(r)
+            return True
+        if r.status == "running":
+            r.status = "cancelled"
+            return True
+        return False
+
+    def _expire(self) -> None:
+        now = self.now()
+        if not any(r.deadline is not None and r.deadline < now for r in self.queue):
+            return
+        keep = collections.deque()
+        for r in self.queue:
+            if r.deadline is not None and r.deadline < now:
+                r.status = "expired"
+                self.expired.append(r)
+            else:
+                keep.append(r)
+        self.queue = keep
 
     def _admit(self) -> list[Request]:
         batch, nbytes = [], 0
@@ -169,11 +205,18 @@ class Server:
                     # the batch's output did not fit (nothing was written): run
                     # its queries again, each with at least its exact count
                     for r, c in reversed(list(zip(f.reqs, counts))):
+                        if r.status == "cancelled":
+                            self.cancelled.append(r)
+                            continue
                         r.capacity, r.retries = max(r.capacity, c), r.retries + 1
+                        r.status = "queued"
                         self.queue.appendleft(r)
                 else:
                     for r, c, h in zip(f.reqs, counts, hits):
-                        r.count, r.hits, r.done = c, h, t
+                        if r.status == "cancelled":
+                            self.cancelled.append(r)
+                            continue
+                        r.count, r.hits, r.done, r.status = c, h, t, "done"
                         self.done.append(r)
                         finished += 1
                 self.free_slots.append(f.slot)
@@ -181,6 +224,7 @@ class Server:
             else:
                 still.append(f)
         self.flights = still
+        self._expire()
         while self.free_slots and self.queue:
             batch = self._admit()
             if not batch:
@@ -188,7 +232,7 @@ class Server:
             slot = self.free_slots.pop()
             t = self.now()
             for r in batch:
-                r.start = t
+                r.start, r.status = t, "running"
             nbytes = self.backend.bytes_for(batch, self.n)
             handle = self.backend.launch(batch, slot)
             self.flights.append(_Flight(slot, batch, handle, nbytes))
@@ -241,6 +285,8 @@ def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
         "batches": server.batches,
         "max_concurrent_batches": server.max_inflight,
         "retries": sum(r.retries for r in server.done),
+        "cancelled": len(server.cancelled),
+        "expired": len(server.expired),
         "queue_depth_mean": depth_area / t_prev if t_prev > 0 else 0.0,
         "queue_depth_max": depth_max,
     }

@@ -147,3 +147,34 @@ def test_queue_depth_reported_and_grows_under_overload():
     st = serve.run_trace(srv, qs)
     assert st["completed"] == 40
     assert st["queue_depth_max"] >= 10 and st["queue_depth_mean"] > 1.0
+
+
+def test_cancel_queued_and_running_queries():
+    text = synth.markov_text(50_000, seed=24)
+    be = FakeBackend(text, delay=0.05)
+    srv = serve.Server(be, n=text.size, slots=1, max_batch=1, mem_budget=1 << 40)
+    a = srv.submit("ACGTACGT", 1)
+    b = srv.submit("TTGACCAA", 1)
+    c = srv.submit("GGCCAATT", 0)
+    srv.step()                      # a starts; b and c wait
+    assert a.status == "running" and b.status == "queued"
+    assert srv.cancel(b) and b.status == "cancelled"
+    assert srv.cancel(a)            # running: its results will be dropped
+    srv.drain(poll=0.001)
+    launched = [q for batch in be.launched for q in batch]
+    assert b.qid not in launched and a.qid in launched
+    assert [r.qid for r in srv.done] == [c.qid]
+    assert {r.qid for r in srv.cancelled} == {a.qid, b.qid}
+    assert not srv.cancel(c)        # already finished
+
+
+def test_queries_past_their_deadline_expire_unstarted():
+    text = synth.markov_text(50_000, seed=25)
+    be = FakeBackend(text, delay=0.03)
+    srv = serve.Server(be, n=text.size, slots=1, max_batch=1, mem_budget=1 << 40)
+    rs = [srv.submit("ACGTACGT", 1, timeout=0.05) for _ in range(8)]
+    srv.drain(poll=0.001)
+    launched = {q for batch in be.launched for q in batch}
+    assert len(srv.expired) > 0 and len(srv.done) + len(srv.expired) == 8
+    assert all(r.qid not in launched and r.status == "expired" for r in srv.expired)
+    assert all(r.status == "done" for r in srv.done)
