@@ -61,3 +61,41 @@ def test_status_codes_instead_of_faults(pm):
         pm.pm_encode_text(b"ACGTX")
     assert e.value.status == pm.PM_E_SYMBOL
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("batch", (None, {}))
+def test_outputs_are_written_within_their_bounds(pm, batch):
+    """Canary records after the capacity and after offsets[npat] stay as
+    they were: the kernels write nothing past what the call was given, also
+    when the output does not fit."""
+    import torch
+    rng = np.random.default_rng(8)
+    text = synth.markov_text(3 * 4096 * 32 + 5, seed=8)
+    t = pm.pm_encode_text(text)
+    pats = [synth.random_pattern(m, m // 10, rng) for m in (12, 40, 90)]
+    ks = [2, 6, 14]
+    cps = [pm.pm_compile_pattern(p) for p in pats]
+    total = pm.pm_search(t, cps, ks).total
+    for cap in (total, total + 10, max(total // 2, 1)):
+        pad = 257
+        hits = torch.full((cap + pad, 2), -7, dtype=torch.int32, device="cuda")
+        offs = torch.full((len(cps) + 1 + pad,), -9, dtype=torch.int64, device="cuda")
+        L = pm.lib()
+        import ctypes
+        harr = (ctypes.c_void_p * len(cps))(*[c.handle for c in cps])
+        karr = (ctypes.c_int32 * len(ks))(*ks)
+        bopts = pm._native.pm_batch_options() if batch is not None else None
+        opts = pm._native.pm_options(0, 0, None, ctypes.pointer(bopts) if bopts is not None else None)
+        needed = ctypes.c_uint64(0)
+        st = L.pm_search_ex(t.handle, harr, len(cps), karr, ctypes.c_void_p(hits.data_ptr()), cap,
+                            ctypes.c_void_p(offs.data_ptr()), ctypes.byref(needed), ctypes.byref(opts),
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        torch.cuda.synchronize()
+        assert needed.value == total
+        assert st == (0 if total <= cap else pm.PM_E_OVERFLOW)
+        assert (hits[cap:] == -7).all()
+        if total > cap:
+            assert (hits[:cap] == -7).all()       # nothing written when the output does not fit
+        else:
+            assert (hits[total:cap] == -7).all()  # nothing past the hits found
+        assert (offs[len(cps) + 1:] == -9).all()
