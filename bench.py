@@ -71,6 +71,8 @@ def args_():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=GENOME_N, help="text length per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched: built-in options and variant table (no tuning launches)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--variant", type=int, default=0)
@@ -547,8 +549,12 @@ def run_batched(a):
     # both measured on this GPU (or read from the tuning cache)
     from paper_1611_06115_gb300 import tune
     t0 = time.perf_counter()
-    tv = tune.tune_variants(text, kmax=64)
-    tb = tune.tune_batch(text, cps, ks, cap, sample=256)
+    if a.no_tune:
+        tv = {"cached": None, "table": pm.pm_get_auto_variants()}
+        tb = {"options": {}, "cached": None, "key": None, "log": [], "checked": None}
+    else:
+        tv = tune.tune_variants(text, kmax=64)
+        tb = tune.tune_batch(text, cps, ks, cap, sample=256)
     tune_s = time.perf_counter() - t0
     g = pm.GraphedBatch(pm.Batch(text, cps, ks, capacity=cap, **tb["options"]))
 
