@@ -200,6 +200,26 @@ def oracle_sample(n: int, pats, budget_s: float, threads: int):
     return S, t, cells(S, ents) / t
 
 
+def host_cpu() -> str:
+    """Architecture and model of the host cores, from /proc/cpuinfo where it
+    names one (x86 'model name'; Arm 'CPU implementer'/'CPU part' codes)."""
+    import platform
+    desc = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = {}
+            for line in f:
+                k, _, v = line.partition(":")
+                info.setdefault(k.strip(), v.strip())
+        if info.get("model name"):
+            desc += " " + info["model name"]
+        elif info.get("CPU part"):
+            desc += f" implementer {info.get('CPU implementer', '?')} part {info['CPU part']}"
+    except OSError:
+        pass
+    return desc
+
+
 # ---------------------------------------------------------------- our arm ---
 
 def run_ours(a):
@@ -449,10 +469,13 @@ def run_ours(a):
     }
     if rank == 0 and world == 1 and a.cpu_seconds > 0:
         S, t, v = oracle_sample(n, pats, a.cpu_seconds, os.cpu_count() or 1)
+        S1, t1, v1 = oracle_sample(n, pats, a.cpu_seconds / 4, 1)
         line["cpu_baseline"] = {"value": v, "unit": "window-cells/s", "cores": os.cpu_count(),
-                                "kind": "oracle",
+                                "kind": "oracle", "cpu": host_cpu(),
                                 "sample": f"first {S} symbols of the same text, all nine "
-                                          f"(pattern, k) searches, {t:.1f} s"}
+                                          f"(pattern, k) searches, {t:.1f} s",
+                                "single_thread": {"value": v1, "unit": "window-cells/s",
+                                                  "sample": f"first {S1} symbols, {t1:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -519,7 +542,7 @@ def run_reference(a):
                                "k in {0,4,16}; 9 searches per step",
                    "sample_symbols": S},
         "cpu_baseline": {"value": v, "unit": "window-cells/s", "cores": threads, "kind": "oracle",
-                         "sample": f"first {S} symbols per step"},
+                         "cpu": host_cpu(), "sample": f"first {S} symbols per step"},
         "e2e": {"value": v, "unit": "window-cells/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -436,15 +436,16 @@ const void *batched_kernel(int ws_max)
 
 int batched_grid(int device, int ws_max)
 {
-    static int cache[64][8] = {};
+    static std::atomic<int> cache[64][8];  // 0 = not yet computed
     if (device < 0 || device >= 64) return 0;
     const int slot = ws_max < 0 ? 0 : (ws_max > 6 ? 6 : ws_max);
-    if (cache[device][slot]) return cache[device][slot];
+    if (const int g = cache[device][slot].load(std::memory_order_relaxed)) return g;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(slot), kScanThreads, 0);
-    cache[device][slot] = sms * (per_sm < 1 ? 1 : per_sm);
-    return cache[device][slot];
+    const int g = sms * (per_sm < 1 ? 1 : per_sm);
+    cache[device][slot].store(g, std::memory_order_relaxed);
+    return g;
 }
 
 }  // namespace

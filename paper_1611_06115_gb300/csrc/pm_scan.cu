@@ -254,20 +254,20 @@ void get_auto_variants(int device, Variant *table)
 
 int scan_grid_limit(Variant v, int32_t k, int device)
 {
-    static int cache[64][kWsMaxK + 4] = {};
+    static std::atomic<int> cache[64][kWsMaxK + 4];  // 0 = not yet computed
     if (device < 0 || device >= 64) return 0;
     v = resolve_variant(v, k);
     const int slot = v == Variant::kWindowSliced     ? k
                      : v == Variant::kPatternSliced  ? kWsMaxK + 1
                      : v == Variant::kPatternSliced2 ? kWsMaxK + 2
                                                      : kWsMaxK + 3;
-    if (cache[device][slot]) return cache[device][slot];
+    if (const int g = cache[device][slot].load(std::memory_order_relaxed)) return g;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(v, k), kScanThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    cache[device][slot] = sms * per_sm;
-    return cache[device][slot];
+    cache[device][slot].store(sms * per_sm, std::memory_order_relaxed);
+    return sms * per_sm;
 }
 
 cudaError_t launch_scan(Variant v, const uint2 *planes, const uint32_t *unk, const PatDesc &d,
