@@ -190,11 +190,11 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
             uint32_t lo[4], hi[4], lo1[4], hi1[4];
 #pragma unroll
             for (uint32_t q = 0; q < 4; ++q) {
-                lo[q] = __funnelshift_r(ta.x, tb.x, 4 * j + q);
-                hi[q] = __funnelshift_r(ta.y, tb.y, 4 * j + q);
+                lo[q] = __funnelshift_r(ta.x, tb.x, 8 * q + j);
+                hi[q] = __funnelshift_r(ta.y, tb.y, 8 * q + j);
                 if (C == 2) {
-                    lo1[q] = __funnelshift_r(tb.x, c.x, 4 * j + q);
-                    hi1[q] = __funnelshift_r(tb.y, c.y, 4 * j + q);
+                    lo1[q] = __funnelshift_r(tb.x, c.x, 8 * q + j);
+                    hi1[q] = __funnelshift_r(tb.y, c.y, 8 * q + j);
                 }
             }
 #pragma unroll
@@ -213,7 +213,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 v = mad_lo(gm[2], m16, v);
                 v = mad_lo(gm[1], m8, v);
                 v = mad_lo(gm[0], m1, v);
-                // window 4j + q goes to bit 8q + j
+                // window 8q + j: bit 7 of byte q goes to bit 8q + j
                 acc[p] |= (v >> (7 - j)) & (0x01010101u << j);
             }
         }
@@ -224,7 +224,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 const PatDesc &d = ba.pats[pi];
                 const uint32_t valid = valid_mask(blk, d.nwin);
                 const uint4 *M = ba.arena + d.masks;
-                uint32_t pass = acc[p] ? untranspose(acc[p]) & valid : 0u;
+                uint32_t pass = acc[p] & valid;
                 if (d.nchunks > (uint32_t)C)
                     pass = settle_staged(pass, blk, ta, tb, stage + 32 * g + lane + 2, M, d.nchunks,
                                          kp, ba.planes);

@@ -20,8 +20,9 @@
 //    of one word by multiply-adds (FMA pipe) together with k in every byte;
 //    bit 5 of a byte is then set exactly when g + k >= 32, i.e. when the
 //    window has at most k mismatches, and two ALU steps move those four bits
-//    into the lane's pass mask (in a transposed bit order, undone only when
-//    a window passes).  Windows that pass with m > 32 are settled: counted
+//    into the lane's pass mask (the word packs windows j, 8+j, 16+j, 24+j,
+//    so each bit lands on its window's own position).  Windows that pass
+//    with m > 32 are settled: counted
 //    one at a time, the first two chunks from the still-staged tile, until
 //    their sum exceeds k or the pattern ends.
 //  * pattern-sliced over 64 positions (k <= 63): the same byte test over two

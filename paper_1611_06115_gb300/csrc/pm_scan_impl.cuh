@@ -86,27 +86,15 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
     return r;
 }
 
-// The pass masks below use a transposed bit order: window 4j + b of the lane
-// sits at bit 8b + j.  This restores the natural order (window w at bit w).
-__device__ __forceinline__ uint32_t untranspose(uint32_t t)
-{
-    uint32_t r = 0;
-    while (t) {
-        const uint32_t p = __ffs(t) - 1;
-        t &= t - 1;
-        r |= 1u << (4 * (p & 7) + (p >> 3));
-    }
-    return r;
-}
-
 // Pattern-sliced test of the first C chunks (C = 1 or 2) for one lane's 32
-// windows; transposed pass mask of the windows with at most k mismatches in
-// positions 0..32C-1 (k <= 32C-1).  Blocks blk, blk+1 (and blk+2 for C = 2)
-// are a, b, c; M0, M1 the masks of chunks 0 and 1.  Every byte of the
-// multiply-add result holds matches + k, below 2^(5+C) so bytes never
-// carry: its bit 4+C is set exactly when matches + k >= 32C,
-// i.e. when the window has at most k mismatches.  k4 = k in every byte;
-// one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
+// windows; pass mask (window w at bit w) of the windows with at most k
+// mismatches in positions 0..32C-1 (k <= 32C-1).  Blocks blk, blk+1 (and
+// blk+2 for C = 2) are a, b, c; M0, M1 the masks of chunks 0 and 1.  Step j
+// takes windows j, 8 + j, 16 + j, 24 + j, one per byte of a multiply-add
+// result that holds matches + k, below 2^(5+C) so bytes never carry: its
+// bit 4+C is set exactly when matches + k >= 32C, i.e. when the window has
+// at most k mismatches, and moves to bit 8q + j, the window's own bit.
+// k4 = k in every byte; one, m8, m16, m24 = 1, 2^8, 2^16, 2^24.
 template <int C>
 __device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint2 c, uint4 M0,
                                                         uint4 M1, uint32_t k4, uint32_t one,
@@ -120,7 +108,7 @@ __device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint2 
         uint32_t g[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int w = 4 * j + q;
+            const int w = 8 * q + j;
             g[q] = __popc(class_match(__funnelshift_r(a.x, b.x, w), __funnelshift_r(a.y, b.y, w), M0));
             if constexpr (C == 2)
                 g[q] += __popc(class_match(__funnelshift_r(b.x, c.x, w), __funnelshift_r(b.y, c.y, w), M1));
@@ -129,7 +117,7 @@ __device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint2 
         v = mad_lo(g[2], m16, v);
         v = mad_lo(g[1], m8, v);
         v = mad_lo(g[0], one, v);
-        // bit kBit of byte q: g[q] + k >= 32C; move bits 8q + kBit to 8q + j
+        // bit kBit of byte q: g[q] + k >= 32C; move bits 8q + kBit to 8q + j = w
         const uint32_t s = j <= kBit ? v >> (kBit - j) : v << (j - kBit);
         pass |= s & (0x01010101u << j);
     }
@@ -417,8 +405,8 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
             uint32_t t = 0u;
             if (valid[g]) {
                 const uint2 c = C == 2 ? stage[32 * g + lane + 2] : make_uint2(0u, 0u);
-                t = untranspose(pass_pattern_sliced<C>(a[g], b[g], c, M0, M1, pc.k4, pc.one, pc.m8,
-                                                       pc.m16, pc.m24)) & valid[g];
+                t = pass_pattern_sliced<C>(a[g], b[g], c, M0, M1, pc.k4, pc.one, pc.m8, pc.m16,
+                                           pc.m24) & valid[g];
             }
             pass[g] = t;
         }
