@@ -79,7 +79,7 @@ def args_():
     ap.add_argument("--workload", choices=("genome", "batched", "serving", "large", "profile"),
                     default="genome",
                     help="genome (the default line); batched and serving print their own "
-                         "lines; profile runs four single searches for an ncu capture")
+                         "lines; profile runs five single searches for an ncu capture")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: queries per second")
     ap.add_argument("--serve-mode", choices=("one-launch", "launch-per-query"), default="launch-per-query",
