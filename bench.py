@@ -73,6 +73,8 @@ def args_():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-tune", action="store_true",
                     help="batched: built-in options and variant table (no tuning launches)")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="reference arm: target seconds of oracle work for the whole run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--variant", type=int, default=0)
@@ -508,7 +510,7 @@ def run_reference(a):
     pats = genome_patterns()
     ents = entries(pats)
     threads = os.cpu_count() or 1
-    budget = 150.0  # seconds for the whole run
+    budget = a.ref_seconds  # seconds for the whole run
     steps_total = a.steps + max(a.warmup, 3)
     S0 = 2_000_000
     txt0 = synth.markov_text(S0, TEXT_SEED)
