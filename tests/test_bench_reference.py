@@ -36,3 +36,20 @@ def test_reference_arm_two_ranks_one_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_cpu_baseline_fields():
+    """The CPU baseline beside the GPU line: the oracle on all cores and on
+    one, with window-cells/s, Gbp/s, the core count and the host CPU."""
+    sys.path.insert(0, ROOT)
+    import bench
+    pats = bench.genome_patterns()
+    d = bench.cpu_baseline(300_000, pats, 0.2)
+    assert d["kind"] == "oracle" and d["unit"] == "window-cells/s" and d["cores"] >= 1
+    assert d["value"] > 0 and d["gbp_per_s"] > 0 and d["cpu"]
+    one = d["single_thread"]
+    assert one["value"] > 0 and one["gbp_per_s"] > 0
+    # window-cells per symbol searched: the nine searches' mean pattern length
+    ents = bench.entries(pats)
+    mean_m = sum(len(p) for p, _ in ents) / len(ents)
+    assert abs(d["value"] / (d["gbp_per_s"] * 1e9) - mean_m) < 0.01 * mean_m
