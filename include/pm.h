@@ -393,12 +393,17 @@ pm_status pm_check_bounded_wait(uint64_t limit_ns, int32_t arrive, uint32_t *tim
  * no counterpart (its timings are of a CPU program).
  *
  * op        0 LOP3 (three-input logic), 1 SHF (funnel shift), 2 POPC,
- *           3 IMAD (integer multiply-add).
+ *           3 IMAD (integer multiply-add); the integer tensor-core forms of
+ *           sm_103a: 4 mma.sync m16n8k32 s8 x s8 -> s32, 5 mma.sync
+ *           m16n8k256 b1 AND-popcount -> s32, 6 the same with k = 128 (the
+ *           1-bit form counts set bits of row AND column: with one-hot text
+ *           rows and class-mask columns, Eq. 4's matches over K/4 positions).
  * iters     loop trips per thread (each trip issues 8 instructions of the kind).
- * Outputs   instructions per second over the whole GPU; the SM clock during
- *           the run in MHz (cycle counter against the global timer); and
- *           instructions per clock per SM (per-thread instructions: 32 per
- *           warp instruction).  Allocates a small buffer; synchronises.
+ * Outputs   instructions per second over the whole GPU (for ops 4..6:
+ *           operations, 2 x M x N x K per warp-wide MMA); the SM clock during
+ *           the run in MHz (cycle counter against the global timer); and the
+ *           same per clock per SM (per-thread instructions: 32 per warp
+ *           instruction).  Allocates a small buffer; synchronises.
  */
 pm_status pm_measure_int_pipe(int32_t op, uint32_t iters, double *ops_per_s, double *sm_mhz,
                               double *ops_per_clk_per_sm);

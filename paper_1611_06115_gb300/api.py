@@ -342,7 +342,7 @@ class GraphedBatch:
         return self.out
 
 
-INT_OPS = ("LOP3", "SHF", "POPC", "IMAD")
+INT_OPS = ("LOP3", "SHF", "POPC", "IMAD", "MMA_S8_M16N8K32", "MMA_B1_M16N8K256", "MMA_B1_M16N8K128")
 
 
 def pm_set_auto_variants(variant_for_k) -> None:

@@ -41,10 +41,10 @@ struct pm_pattern {
     uint32_t unknown;  // symbols coded "-" because Table 2 does not list them
     uint4 *masks;      // host, nchunks entries
     // The first min(m, 32) positions as a list for the window-sliced scan:
-    // n_single entries {shift j, X, Y, 0} for one-letter classes (X, Y the
-    // letter's code bits broadcast to whole words), then n_general pairs
-    // {j, 0, 0, 0}, {A, C, G, T} (membership broadcast) for the other
-    // classes; N (every letter) is left out because it never mismatches.
+    // n_single entries {shift j, letter code, 0, 0} for one-letter classes
+    // (Table 1 codes A=0 C=1 G=2 T=3), then n_general pairs {j, 0, 0, 0},
+    // {A, C, G, T} (membership broadcast) for the other classes; N (every
+    // letter) is left out because it never mismatches.
     uint32_t n_single;
     uint32_t n_general;
     uint4 *wslist;     // host, n_single + 2 * n_general entries
@@ -64,9 +64,11 @@ struct TraceRange {
 // The window-sliced list of p (see pm_pattern) reordered for text t so that
 // windows die as early as possible (the early stop of Sec. 2.4 then ends the
 // scan sooner; the sum of Eq. 4 does not depend on the order): one-letter
-// entries by increasing frequency of their letter in t, then the class
-// entries by increasing frequency of their letters.  Stable; out receives
-// n_single + 2 * n_general entries.
+// entries by increasing frequency of their letter in t (ties by letter, so
+// that each letter's entries form one run; every entry's z field receives
+// the index one past the end of its run), then the class entries by
+// increasing frequency of their letters.  Stable; out receives n_single +
+// 2 * n_general entries.
 inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
 {
     const uint32_t ns = p->n_single, ng = p->n_general;
@@ -75,7 +77,7 @@ inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
     for (uint32_t i = 0; i < ns; ++i) {
         const uint4 e = p->wslist[i];
         idx[i] = i;
-        key[i] = t->count[(e.y & 1u) | ((e.z & 1u) << 1)];
+        key[i] = (t->count[e.y & 3u] << 2) | (e.y & 3u);  // counts < 2^32
     }
     for (uint32_t i = 0; i < ng; ++i) {
         const uint4 mem = p->wslist[ns + 2 * i + 1];
@@ -94,6 +96,8 @@ inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
     sort_range(0, ns);
     sort_range(ns, ns + ng);
     for (uint32_t i = 0; i < ns; ++i) out[i] = p->wslist[idx[i]];
+    for (uint32_t i = ns; i-- > 0;)
+        out[i].z = (i + 1 < ns && out[i + 1].y == out[i].y) ? out[i + 1].z : i + 1;
     for (uint32_t i = 0; i < ng; ++i) {
         out[ns + 2 * i] = p->wslist[ns + 2 * idx[ns + i]];
         out[ns + 2 * i + 1] = p->wslist[ns + 2 * idx[ns + i] + 1];
@@ -105,6 +109,7 @@ constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kGroups = 4;                               // 32-window groups per lane per tile
 constexpr uint64_t kTileWindows = 32ull * 32 * kGroups;  // one warp tile: 4096 windows
 constexpr int kStageBlocks = 32 * kGroups + 2;           // a warp tile's blocks + 2 halo blocks
+constexpr uint32_t kStages = 3;                          // tiles a scan warp keeps staged or in flight
 constexpr uint32_t kStageBytes = kStageBlocks * 8;       // one bulk copy per warp tile
 constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
 constexpr uint64_t kWaitLimitNs = 1000000000ull;         // bounded device waits: 1 s

@@ -139,12 +139,13 @@ pm_status pm_compile_pattern(const char *iupac, uint32_t m, pm_pattern **out)
         delete p;
         return PM_E_NOMEM;
     }
-    // one-letter classes first (the most selective), each as its code bits
+    // one-letter classes first (the most selective), each as its letter's
+    // Table 1 code (the end of its run is set when the list is ordered)
     for (uint32_t j = 0; j < head; ++j) {
         const uint8_t mask = tab.mask[(unsigned char)iupac[j]];
         if (__builtin_popcount(mask) != 1) continue;
         const uint32_t code = (uint32_t)__builtin_ctz(mask);  // A=0 C=1 G=2 T=3
-        p->wslist[p->n_single++] = make_uint4(j, 0u - (code & 1u), 0u - (code >> 1), 0u);
+        p->wslist[p->n_single++] = make_uint4(j, code, 0u, 0u);
     }
     // then the other classes except N (which never mismatches), as membership words
     for (uint32_t j = 0; j < head; ++j) {

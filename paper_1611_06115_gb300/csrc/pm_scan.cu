@@ -4,12 +4,15 @@
 // Work unit: a warp tile of kGroups x 32 consecutive 32-symbol blocks.  Lane l
 // owns the 32 windows that start in block 32g + l of the tile, for each group
 // g.  Windows need at most m-1 symbols beyond their tile (the overlap of
-// Sec. 2.6): the tile and a 2-block halo arrive in shared memory by one bulk
-// (TMA) copy, issued by the warp itself two tiles ahead into a two-stage
-// ring with one mbarrier per stage; deeper blocks, read only by the rare
-// windows still alive after 32 positions, come through L1/L2.  Warps never
-// wait for each other: each persistent warp walks its own tiles, and a
-// tile's hits are emitted by a warp-aggregated atomic.
+// Sec. 2.6): the tile and a 2-block halo arrive in shared memory by 16-byte
+// asynchronous copies (cp.async) that the warp's lanes issue kStages tiles
+// ahead into a ring of stages; deeper blocks, read only by the rare windows
+// still alive after 64 positions, come through L1/L2.  (One bulk copy per
+// warp tile, the tile's 1040 bytes through the TMA unit, streamed the text
+// at 2.7 TB/s on GB300 whatever the depth of the ring; the lanes' own copies
+// stream it at 5.7 TB/s.)  Warps never wait for each other: each persistent
+// warp walks its own tiles, and a tile's hits are emitted by a
+// warp-aggregated atomic.
 //
 // Four evaluations, all exact, chosen per k (a measured table per device):
 //
@@ -56,19 +59,27 @@ using namespace scan;
 // positions 0..63 (k <= 63), -2 pattern-sliced over all chunks (any k); K in
 // 0..kWsMaxK window-sliced with threshold K.  The -2 kernel keeps 32 running
 // counts per lane in registers, so it takes twice the registers at half the
-// resident warps.
+// resident warps; the window-sliced kernels with K >= 3 keep K+1 counter
+// words per group and run three CTAs per SM.
+//
+// Each warp stages its tiles kStages strides ahead, one commit group of
+// asynchronous copies per tile (an empty group once the tiles run out, so
+// that group i always belongs to the warp's i-th tile); a stage is refilled
+// once its tile is done (settling and hit counts read the staged tile).
+// Tile indices fit in 32 bits: a text has fewer than 2^32 symbols.
 template <int VARIANT>
-__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
+__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 3 ? 3 : 4))
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status,
            const uint32_t *__restrict__ unk)
 {
     constexpr bool kWS = VARIANT >= 0;
+    constexpr uint32_t S = kStages;
 
-    __shared__ __align__(128) uint2 sbuf[kScanWarps][2][kStageBlocks];
-    __shared__ __align__(8) uint64_t sbar[kScanWarps][2];
+    __shared__ __align__(128) uint2 sbuf[kScanWarps][S][kStageBlocks];
     __shared__ uint4 slist[kWS ? 64 : 1];
+    __shared__ uint32_t squeue[kScanWarps][kQueueCap];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -81,83 +92,72 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : 4)
         for (uint32_t i = threadIdx.x; i < len; i += kScanThreads) slist[i] = __ldg(arena + d.wslist + i);
         __syncthreads();  // the only CTA-wide barrier: the list is shared by all warps
     }
-    if (lane == 0) {
-        dev::mbar_init(&sbar[warp][0], 1);
-        dev::mbar_init(&sbar[warp][1], 1);
-        dev::fence_mbar_init();
-    }
-    __syncwarp();
-
-    const uint64_t stride = (uint64_t)gridDim.x * kScanWarps;
-    const uint64_t first = (uint64_t)blockIdx.x * kScanWarps + warp;
-    if (lane == 0) {
-        if (first < d.ntiles) issue_tile(planes, first, &sbuf[warp][0][0], &sbar[warp][0]);
-        if (first + stride < d.ntiles)
-            issue_tile(planes, first + stride, &sbuf[warp][1][0], &sbar[warp][1]);
-    }
-
-    uint32_t it = 0;
-    for (uint64_t tile = first; tile < d.ntiles; tile += stride, ++it) {
-        const int s = it & 1;
-        const bool ok = dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
-        if (__any_sync(kFull, !ok)) {
-            if (lane == 0) {
-                atomicOr(status, kDevTimeout);
-                // let the copies this warp still has in flight land before it leaves
-                dev::mbar_wait_bounded(&sbar[warp][s], (it >> 1) & 1u, kWaitLimitNs);
-                if (tile + stride < d.ntiles)
-                    dev::mbar_wait_bounded(&sbar[warp][s ^ 1], ((it + 1) >> 1) & 1u, kWaitLimitNs);
-            }
-            return;
-        }
-        uint2 a[G], b[G];
+    const uint32_t ntiles = (uint32_t)d.ntiles;
+    const uint32_t nfull = (uint32_t)(d.nwin / kTileWindows);  // tiles whose windows are all valid
+    const uint32_t stride = gridDim.x * kScanWarps;
+    const uint32_t first = blockIdx.x * kScanWarps + warp;
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            a[g] = sbuf[warp][s][32 * g + lane];
-            b[g] = sbuf[warp][s][32 * g + lane + 1];
-        }
-        // The pattern-sliced evaluation (k <= 31) still reads the staged tile
-        // while it settles the windows that survive the first 32 positions,
-        // so it refills the stage after the tile; the others refill it now.
-        constexpr bool kLateRefill = VARIANT == -1 || VARIANT == -3;
-        if constexpr (!kLateRefill) {
-            __syncwarp();
-            if (lane == 0 && tile + 2 * stride < d.ntiles) {
-                dev::fence_proxy_async_smem();
-                issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
-            }
-        }
+    for (uint32_t st = 0; st < S; ++st) {
+        if (first + st * stride < ntiles) copy_tile_async(planes, first + st * stride, &sbuf[warp][st][0], lane);
+        cp_async_commit();
+    }
 
-        uint64_t blk[G];
+    uint32_t s = 0;
+    for (uint32_t tile = first; tile < ntiles; tile += stride) {
+        cp_async_wait<S - 1>();  // this tile's group has landed (later ones may be pending)
+        __syncwarp();            // ... for every lane's pieces
+        const uint2 *stage = &sbuf[warp][s][0];
+        uint2 a[G], b[G];
         uint32_t valid[G], pass[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;  // windows start at 32*blk
-            valid[g] = valid_mask(blk[g], d.nwin);
+            a[g] = stage[32 * g + lane];
+            b[g] = stage[32 * g + lane + 1];
         }
-        tile_pass<VARIANT>(a, b, blk, valid, d, M, M0, slist, pc, planes, &sbuf[warp][s][0], pass);
-        if constexpr (kLateRefill) {
-            __syncwarp();
-            if (lane == 0 && tile + 2 * stride < d.ntiles) {
-                dev::fence_proxy_async_smem();
-                issue_tile(planes, tile + 2 * stride, &sbuf[warp][s][0], &sbar[warp][s]);
-            }
+        if (tile < nfull) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) valid[g] = kFull;
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g) valid[g] = valid_mask((uint64_t)tile * (32u * G) + 32u * g + lane, d.nwin);
         }
+        const bool need = tile_first_stage<VARIANT>(a, b, tile, valid, d, M, M0, slist, pc, planes, stage, pass);
 
-        // ---- hits of this warp tile, in window order (warp-aggregated atomic) ----
+        // ---- exact counts and hits of this warp tile, in window order ----
         uint32_t anyp = 0;
 #pragma unroll
         for (int g = 0; g < G; ++g) anyp |= pass[g];
+        TileEntry *entry = table + d.tile0 + tile;
         if (__any_sync(kFull, anyp != 0u)) {
-            uint32_t total;
-            unsigned long long base;
-            emit_tile_hits<kLateRefill>(pass, blk, a, b, M0, d, M, planes, unk, tmp, cap, cursor, total,
-                                        base);
-            if (lane == 0) table[d.tile0 + tile] = TileEntry{total, (uint32_t)base};
+            if (!settle_emit_queued(pass, tile, stage, squeue[warp], d, M, planes, unk, tmp, cap, cursor,
+                                    entry)) {
+                // more candidates than the queue holds (dense hits): each lane its own
+                uint64_t blk[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) blk[g] = (uint64_t)tile * (32u * G) + 32u * g + lane;
+                settle_dense<VARIANT>(need, a, b, blk, d, M, planes, stage, pass);
+                anyp = 0;
+#pragma unroll
+                for (int g = 0; g < G; ++g) anyp |= pass[g];
+                if (__any_sync(kFull, anyp != 0u)) {
+                    uint32_t total;
+                    unsigned long long base;
+                    emit_tile_hits<true>(pass, blk, a, b, M0, d, M, planes, unk, tmp, cap, cursor, total, base);
+                    if (lane == 0) *entry = TileEntry{total, (uint32_t)base};
+                } else if (lane == 0) {
+                    *entry = TileEntry{0u, 0u};
+                }
+            }
         } else if (lane == 0) {
-            table[d.tile0 + tile] = TileEntry{0u, 0u};
+            *entry = TileEntry{0u, 0u};
         }
+        // refill this stage with the tile S strides ahead
+        __syncwarp();  // every lane is done reading the stage
+        if (tile + S * stride < ntiles) copy_tile_async(planes, tile + S * stride, &sbuf[warp][s][0], lane);
+        cp_async_commit();
+        if (++s == S) s = 0;
     }
+    cp_async_wait<0>();  // nothing in flight when the warp leaves
 }
 
 template <int VARIANT>

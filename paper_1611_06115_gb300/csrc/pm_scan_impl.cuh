@@ -141,14 +141,118 @@ __device__ __forceinline__ uint4 ld_list(const uint4 *p)
 // cost 1.4-4x the scan.
 __host__ __device__ constexpr uint32_t ws_cut(int K) { return K == 0 ? 8u : 4u + 2u * (uint32_t)K; }
 
+// Bit i set where symbol i of block t is the letter with Table 1 code CODE
+// (A = 00, C = 01, G = 10, T = 11; t.x holds the low code bits, t.y the high).
+template <int CODE>
+__device__ __forceinline__ uint32_t letter_plane(uint2 t)
+{
+    static_assert(CODE >= 0 && CODE < 4, "Table 1 codes");
+    if constexpr (CODE == 0) return ~(t.x | t.y);
+    else if constexpr (CODE == 1) return t.x & ~t.y;
+    else if constexpr (CODE == 2) return ~t.x & t.y;
+    else return t.x & t.y;
+}
+
+// Thermometer counter of K+1 levels over 32 windows: level i is set once a
+// window has more than i mismatches.  `match` has bit w set where window w
+// matches the position just tested.
+template <int K>
+__device__ __forceinline__ void add_position(uint32_t (&L)[K + 1], uint32_t match)
+{
+#pragma unroll
+    for (int i = K; i >= 1; --i) L[i] |= L[i - 1] & ~match;
+    L[0] |= ~match;
+}
+
+// True when every window of the lane's groups, on every lane, is past K.
+template <int K>
+__device__ __forceinline__ bool all_past(const uint32_t (&L)[G][K + 1])
+{
+    uint32_t d = kFull;
+#pragma unroll
+    for (int g = 0; g < G; ++g) d &= L[g][K];
+    return __all_sync(kFull, d == kFull);
+}
+
+// Outcome of a stretch of the window-sliced scan.
+constexpr int kWsGoOn = 0;  // list not exhausted, some window alive
+constexpr int kWsDead = 1;  // every window past K
+constexpr int kWsCut = 2;   // `cut` entries tested, some window alive
+
+// One run of list entries that share the one-letter class CODE (entries
+// e .. end-1).  The letter's plane is built once per run from the lane's
+// two blocks per group, so each position costs one funnel shift (its match
+// word for 32 windows) and the counter update; K = 0 folds two positions
+// into one update.  The early stop is checked whenever e reaches a multiple
+// of the block size S (2 entries for K = 0 from entry 4 on, else 4), across
+// run boundaries, as if the list were one run.
+template <int K, int CODE, bool kGlobal>
+__device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&b)[G],
+                                             const uint4 *__restrict__ list, uint32_t &e,
+                                             uint32_t end, uint32_t cut, uint32_t (&L)[G][K + 1])
+{
+    uint32_t pa[G], pb[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        pa[g] = letter_plane<CODE>(a[g]);
+        pb[g] = letter_plane<CODE>(b[g]);
+    }
+    constexpr uint32_t S = K == 0 ? 2u : 4u;
+    auto check = [&]() -> int {
+        if (K == 0 && e < 4) return kWsGoOn;
+        if (all_past<K>(L)) return kWsDead;
+        if (e >= cut) return kWsCut;
+        return kWsGoOn;
+    };
+    // single entries up to the next multiple of S
+    while (e < end && (e & (S - 1)) != 0) {
+        const uint32_t s0 = ld_list<kGlobal>(list + e).x;
+#pragma unroll
+        for (int g = 0; g < G; ++g) add_position<K>(L[g], __funnelshift_r(pa[g], pb[g], s0));
+        ++e;
+        if ((e & (S - 1)) == 0) {
+            const int r = check();
+            if (r != kWsGoOn) return r;
+        }
+    }
+    // whole blocks
+    while (e + S <= end) {
+        uint32_t s[S];
+#pragma unroll
+        for (uint32_t u = 0; u < S; ++u) s[u] = ld_list<kGlobal>(list + e + u).x;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if constexpr (K == 0) {
+                L[g][0] |= ~(__funnelshift_r(pa[g], pb[g], s[0]) & __funnelshift_r(pa[g], pb[g], s[1]));
+            } else {
+#pragma unroll
+                for (uint32_t u = 0; u < S; ++u) add_position<K>(L[g], __funnelshift_r(pa[g], pb[g], s[u]));
+            }
+        }
+        e += S;
+        const int r = check();
+        if (r != kWsGoOn) return r;
+    }
+    // the rest of the run (fewer than S entries: no multiple of S is reached)
+    for (; e < end; ++e) {
+        const uint32_t s0 = ld_list<kGlobal>(list + e).x;
+#pragma unroll
+        for (int g = 0; g < G; ++g) add_position<K>(L[g], __funnelshift_r(pa[g], pb[g], s0));
+    }
+    return kWsGoOn;
+}
+
 // Window-sliced first chunk with a thermometer counter of K+1 levels over the
-// listed positions, for all groups of the lane at once.  alive[g] receives
-// the windows still at or below K.  After `cut` list entries (checked every
-// four) the scan stops if some window is still alive and returns true: the
-// few candidates left are cheaper to count one by one (settle_from_regs)
-// than to carry the whole tile through the remaining positions.  Returns
-// false when every listed position was tested (alive is then exact over the
-// first 32 positions) or every window died.
+// listed positions, for all groups of the lane at once.  The list (built by
+// pm_compile_pattern, ordered for the text by the host) holds first the
+// one-letter positions {shift, letter code, end of the run of that letter,
+// 0}, grouped into runs by letter, then pairs {shift, 0, 0, 0}, {A, C, G, T}
+// (membership broadcast) for the other classes.  alive[g] receives the
+// windows still at or below K.  After `cut` list entries the scan stops if
+// some window is still alive and returns true: the few candidates left are
+// cheaper to count one by one than to carry the whole tile through the
+// remaining positions.  Returns false when every listed position was tested
+// (alive is then exact over the first 32 positions) or every window died.
 template <int K, bool kGlobal = false>
 __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
                                                     const uint4 *__restrict__ list,
@@ -161,56 +265,23 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
     for (int g = 0; g < G; ++g)
 #pragma unroll
         for (int i = 0; i <= K; ++i) L[g][i] = ~valid[g];  // invalid windows sit at every level
-    auto dead_all = [&]() {
-        uint32_t d = kFull;
-#pragma unroll
-        for (int g = 0; g < G; ++g) d &= L[g][K];
-        return !__any_sync(kFull, ~d);
-    };
-    auto add = [&](int g, uint32_t mis) {
-#pragma unroll
-        for (int i = K; i >= 1; --i) L[g][i] |= L[g][i - 1] & mis;
-        L[g][0] |= mis;
-    };
     uint32_t e = 0;
-    for (; e + 4 <= n_single; e += 4) {
-        uint4 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = ld_list<kGlobal>(list + e + u);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            uint32_t mis[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q[u].x);
-                const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q[u].x);
-                mis[u] = (lo ^ q[u].y) | (hi ^ q[u].z);
-            }
-            if constexpr (K == 0) {
-                L[g][0] |= (mis[0] | mis[1]) | (mis[2] | mis[3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) add(g, mis[u]);
-            }
+    while (e < n_single) {
+        const uint4 h = ld_list<kGlobal>(list + e);
+        // a run ends past its first entry and inside the list (also for a
+        // malformed list, so that the loop always advances)
+        const uint32_t end = h.z > e ? (h.z < n_single ? h.z : n_single) : e + 1;
+        int r;
+        switch (h.y & 3u) {
+        case 0: r = ws_letter_run<K, 0, kGlobal>(a, b, list, e, end, cut, L); break;
+        case 1: r = ws_letter_run<K, 1, kGlobal>(a, b, list, e, end, cut, L); break;
+        case 2: r = ws_letter_run<K, 2, kGlobal>(a, b, list, e, end, cut, L); break;
+        default: r = ws_letter_run<K, 3, kGlobal>(a, b, list, e, end, cut, L); break;
         }
-        if (dead_all()) {
+        if (r != kWsGoOn) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) alive[g] = 0u;
-            return false;
-        }
-        if (e + 4 >= cut) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
-            return true;
-        }
-    }
-    for (; e < n_single; ++e) {
-        const uint4 q = ld_list<kGlobal>(list + e);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, q.x);
-            const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, q.x);
-            add(g, (lo ^ q.y) | (hi ^ q.z));
+            for (int g = 0; g < G; ++g) alive[g] = r == kWsDead ? 0u : ~L[g][K];
+            return r == kWsCut;
         }
     }
     for (uint32_t c = 0; c < n_general; ++c) {
@@ -220,10 +291,10 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
         for (int g = 0; g < G; ++g) {
             const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, s);
             const uint32_t hi = __funnelshift_r(a[g].y, b[g].y, s);
-            add(g, ~class_match(lo, hi, M));
+            add_position<K>(L[g], class_match(lo, hi, M));
         }
         if ((c & 3) == 3) {
-            if (dead_all()) {
+            if (all_past<K>(L)) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) alive[g] = 0u;
                 return false;
@@ -246,6 +317,36 @@ __device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, u
 {
     dev::mbar_arrive_expect_tx(bar, kStageBytes);
     dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
+}
+
+// One warp tile and its halo, global -> shared, by the warp's own lanes:
+// 16-byte asynchronous copies (cp.async), lane l taking pieces l and l + 32
+// and lane 0 the halo piece, as one commit group per lane.  Both addresses
+// are 16-byte aligned (tiles start at multiples of 1024 bytes).  Complete
+// once every lane has passed cp_async_wait for the group and the warp has
+// synchronised.
+static_assert(kStageBytes == 32 * 2 * 16 + 16, "a warp tile is 64 pieces of 16 bytes plus the halo");
+__device__ __forceinline__ void copy_tile_async(const uint2 *planes, uint32_t tile, uint2 *dst, int lane)
+{
+    const char *src = (const char *)(planes + (uint64_t)tile * (32u * G));
+    const uint32_t d = dev::smem_u32(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * lane), "l"(src + 16 * lane)
+                 : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * (lane + 32)),
+                 "l"(src + 16 * (lane + 32))
+                 : "memory");
+    if (lane == 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 1024u), "l"(src + 1024)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this lane's most recent commit groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 
@@ -366,34 +467,33 @@ __device__ __forceinline__ PsConst ps_const(uint32_t two, uint32_t k)
     return c;
 }
 
-// The windows of one warp tile that hold the pattern with at most k
-// mismatches: pass[g] bit w for window 32*blk[g] + w.  VARIANT as in k_scan;
-// list (window-sliced only) is the pattern's position list in shared memory;
-// stage (pattern-sliced, -1 and -3) is the tile still staged in shared memory.
+// First stage of one warp tile: pass[g] bit w for window 32*blk[g] + w,
+// a superset of the windows of the tile that hold the pattern with at most k
+// mismatches (VARIANT as in k_scan; list is the window-sliced position list
+// in shared memory; stage the tile still staged in shared memory).  Returns
+// true when pass still needs exact counts past the positions tested (see
+// settle_dense or settle_emit_queued); false when pass is exact.
 template <int VARIANT>
-__device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[G],
-                                          const uint64_t (&blk)[G], const uint32_t (&valid)[G],
-                                          const PatDesc &d, const uint4 *__restrict__ M,
-                                          uint4 M0, const uint4 *__restrict__ list,
-                                          const PsConst &pc, const uint2 *__restrict__ planes,
-                                          const uint2 *stage, uint32_t (&pass)[G])
+__device__ __forceinline__ bool tile_first_stage(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                 uint32_t tile, const uint32_t (&valid)[G],
+                                                 const PatDesc &d, const uint4 *__restrict__ M,
+                                                 uint4 M0, const uint4 *__restrict__ list,
+                                                 const PsConst &pc, const uint2 *__restrict__ planes,
+                                                 const uint2 *stage, uint32_t (&pass)[G])
 {
     const uint32_t k = (uint32_t)d.k;
     if constexpr (VARIANT >= 0) {
         const bool cut = alive_window_sliced<VARIANT>(a, b, list, d.n_single, d.n_general, ws_cut(VARIANT),
                                                       valid, pass);
-        if (cut || d.nchunks > 1) {
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                pass[g] = settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, k, planes);
-        }
-        return;
+        return cut || d.nchunks > 1;
     } else if constexpr (VARIANT == -2) {
-        // k > 31: one chunk cannot decide; count all chunks (exact, nothing to settle)
+        // k > 31: one chunk cannot decide; count all chunks (exact)
+        const int lane = threadIdx.x & 31;
 #pragma unroll 1
         for (int g = 0; g < G; ++g)
-            pass[g] = pass_multi_chunk(planes, blk[g], M, d.nchunks, k, valid[g], a[g], b[g]);
-        return;
+            pass[g] = pass_multi_chunk(planes, (uint64_t)tile * (32u * G) + 32u * g + lane, M, d.nchunks, k,
+                                       valid[g], a[g], b[g]);
+        return false;
     } else {
         // -1: one chunk; -3: two chunks (chunk 1 of a pattern with m <= 32
         // reads as all ones: every position past m matches)
@@ -410,19 +510,31 @@ __device__ __forceinline__ void tile_pass(const uint2 (&a)[G], const uint2 (&b)[
             }
             pass[g] = t;
         }
+        return d.nchunks > (uint32_t)C;
     }
-    // Both evaluations are exact for m <= 32.  Longer patterns: count every
-    // remaining window exactly and drop those past k.
-    if (d.nchunks > 1) {
-        const int lane = threadIdx.x & 31;
+}
+
+// Exact counts for pass (when `need`), each lane settling its own windows:
+// the path for tiles with more candidates than settle_emit_queued takes.
+template <int VARIANT>
+__device__ __forceinline__ void settle_dense(bool need, const uint2 (&a)[G], const uint2 (&b)[G],
+                                             const uint64_t (&blk)[G], const PatDesc &d,
+                                             const uint4 *__restrict__ M,
+                                             const uint2 *__restrict__ planes, const uint2 *stage,
+                                             uint32_t (&pass)[G])
+{
+    if (!need) return;
+    const uint32_t k = (uint32_t)d.k;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if constexpr (VARIANT == -1 || VARIANT == -3)
-                pass[g] = settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M,
-                                        d.nchunks, k, planes);
-            else
-                pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
-        }
+    for (int g = 0; g < G; ++g) {
+        if constexpr (VARIANT >= 0)
+            pass[g] = settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, k, planes);
+        else if constexpr (VARIANT == -1 || VARIANT == -3)
+            pass[g] = settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M, d.nchunks,
+                                    k, planes);
+        else
+            pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
     }
 }
 
@@ -493,6 +605,123 @@ __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64
         }
         base += tot[g];
     }
+}
+
+// Candidates a warp settles per tile through its shared-memory queue
+// (settle_emit_queued); tiles with more take settle_dense and emit_tile_hits.
+constexpr uint32_t kQueueCap = 256;
+
+// The count of window 32*blk + w, exact up to k (once past k, some value
+// above k).  kStaged: blocks blk .. blk+2 are still staged in shared memory
+// at stage_blk[0..2], so the first two chunks need no load through L1/L2.
+template <bool kStaged>
+__device__ __forceinline__ uint32_t candidate_count(const uint2 *stage_blk, uint64_t blk, uint32_t w,
+                                                    const uint4 *__restrict__ M, uint32_t nchunks,
+                                                    uint32_t k, const uint2 *__restrict__ planes,
+                                                    const uint32_t *__restrict__ unk)
+{
+    if (unk) return window_count_exact(planes, unk, blk, w, M, nchunks, k);
+    if constexpr (kStaged) {
+        const uint2 t0 = stage_blk[0], t1 = stage_blk[1];
+        uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), __ldg(M)));
+        if (c <= k && nchunks > 1) {
+            const uint2 t2 = stage_blk[2];
+            c += __popc(~class_match(__funnelshift_r(t1.x, t2.x, w), __funnelshift_r(t1.y, t2.y, w),
+                                     __ldg(M + 1)));
+            if (c <= k && nchunks > 2) c = window_count_from(planes, blk, w, M, 2, nchunks, c, k);
+        }
+        return c;
+    } else {
+        return window_count_from(planes, blk, w, M, 0, nchunks, 0u, k);
+    }
+}
+
+// Settle and emit the candidates of one warp tile (cand[g] bit w: window
+// 32*(tile*32G + 32g + lane) + w; the tile still staged at `stage`) with the
+// whole warp working on them together, whichever lanes they came from: the
+// candidates are written, in
+// window order, to the warp's queue q in shared memory (kQueueCap entries);
+// each lane then counts every 32nd of them exactly (up to k), the hits are
+// compacted in place, in window order, and written once to tmp behind one
+// warp-aggregated atomic on cursor (coalesced); *entry receives {hits,
+// first}.  A lane that held candidates in one group of a tile would
+// otherwise keep the other 31 lanes waiting while it counts them one by one.
+// Returns false, having done nothing, when the tile has more than kQueueCap
+// candidates or k >= 2^20 (a count is packed with its window in 32 bits).
+// Call with the whole warp.
+__device__ __forceinline__ bool settle_emit_queued(const uint32_t (&cand)[G], uint32_t tile,
+                                                   const uint2 *stage, uint32_t *q, const PatDesc &d,
+                                                   const uint4 *__restrict__ M,
+                                                   const uint2 *__restrict__ planes,
+                                                   const uint32_t *__restrict__ unk,
+                                                   pm_hit *__restrict__ tmp, uint64_t cap,
+                                                   unsigned long long *__restrict__ cursor,
+                                                   TileEntry *entry)
+{
+    static_assert(G == 4, "one byte per group");
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t k = (uint32_t)d.k;
+    // byte g: this lane's candidates in group g (at most 32 each)
+    uint32_t packed = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) packed |= (uint32_t)__popc(cand[g]) << (8 * g);
+    const uint32_t total = __reduce_add_sync(kFull, (packed * 0x01010101u) >> 24);
+    if (total > kQueueCap || k >= (1u << 20)) return false;
+    // Inclusive scan over the lanes of all four bytes at once: no byte ever
+    // exceeds total <= 255, so bytes never carry into each other.
+    uint32_t incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    // byte g: where this lane's group-g candidates start (all of groups < g,
+    // then those of group g on the lanes before this one)
+    const uint32_t pos = tot * 0x01010100u + (incl - packed);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        uint32_t p = (pos >> (8 * g)) & 0xffu;
+        uint32_t m = cand[g];
+        while (m) {
+            const uint32_t w = __ffs(m) - 1;
+            m &= m - 1;
+            q[p++] = ((uint32_t)g << 10) | (lane << 5) | w;  // window within the tile
+        }
+    }
+    __syncwarp();
+    uint32_t hits = 0;
+    for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint32_t rec = 0;
+        bool hit = false;
+        if (i < total) {
+            const uint32_t e = q[i];
+            const uint32_t gl = e >> 5;  // block within the tile
+            const uint32_t c = candidate_count<true>(stage + gl, (uint64_t)tile * (32u * G) + gl, e & 31u, M,
+                                                     d.nchunks, k, planes, unk);
+            hit = c <= k;
+            rec = e | (c << 12);
+        }
+        const uint32_t hb = __ballot_sync(kFull, hit);
+        __syncwarp();  // every entry of this round is read before any is overwritten
+        if (hit) q[hits + __popc(hb & ((1u << lane) - 1u))] = rec;
+        hits += __popc(hb);
+    }
+    unsigned long long base = 0;
+    if (hits) {
+        __syncwarp();
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)hits);
+        base = __shfl_sync(kFull, base, 0);
+        const uint64_t w0 = (uint64_t)tile * kTileWindows;
+        for (uint32_t i = lane; i < hits; i += 32) {
+            const uint32_t r = q[i];
+            if (base + i < cap) tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & 4095u)), r >> 12};
+        }
+    }
+    if (lane == 0) *entry = TileEntry{hits, (uint32_t)base};
+    __syncwarp();  // the queue is rewritten by the next tile
+    return true;
 }
 
 }  // namespace scan
