@@ -228,7 +228,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 const uint4 *M = ba.arena + d.masks;
                 uint32_t pass = acc[p] & valid;
                 if (d.nchunks > (uint32_t)C)
-                    pass = settle_staged(pass, blk, ta, tb, stage + 32 * g + lane + 2, M, d.nchunks,
+                    pass = settle_staged(pass, blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, d.nchunks,
                                          kp, ba.planes);
                 if (__any_sync(kFull, pass != 0u))
                     emit_group(pass, blk, pi, ((unsigned long long)pi * ba.ntiles + tile) * G + g,

@@ -109,6 +109,7 @@ constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kGroups = 4;                               // 32-window groups per lane per tile
 constexpr uint64_t kTileWindows = 32ull * 32 * kGroups;  // one warp tile: 4096 windows
 constexpr int kStageBlocks = 32 * kGroups + 2;           // a warp tile's blocks + 2 halo blocks
+constexpr int kScanStageBlocks = kStageBlocks + 2;       // per-pattern scan: from an even block
 constexpr uint32_t kStages = 3;                          // tiles a scan warp keeps staged or in flight
 constexpr uint32_t kStageBytes = kStageBlocks * 8;       // one bulk copy per warp tile
 constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
@@ -128,12 +129,13 @@ struct PatDesc {
     uint32_t two;        // the constant 2, given at run time so that the multiply-adds
                          //   built on it stay multiply-adds (FMA pipe)
     uint32_t variant;    // Variant chosen for this pattern (batched kernel)
-    uint32_t pad0;
+    uint32_t c0;         // pattern-sliced scan kernels: the chunk their first stage tests
+                         //   (first_stage_chunk); 0 everywhere else
     uint64_t masks;      // chunk 0 in the arena (uint4 units)
     uint64_t wslist;     // window-sliced list in the arena (uint4 units)
     uint64_t nwin;       // windows: n - m + 1, or 0 when m > n
     uint64_t tile0;      // first tile-table entry of this pattern
-    uint64_t ntiles;     // ceil(nwin / kTileWindows)
+    uint64_t ntiles;     // warp tiles: ceil(nwin / windows per tile of the kernel that runs)
 };
 
 // Hits of one (pattern, warp tile): how many, and where the scan kernel put
@@ -179,6 +181,14 @@ int scan_grid_limit(Variant v, int32_t k, int device);
 // pm_set_auto_variants; already resolved for d.k).
 Variant auto_variant(const PatDesc &d, int device);
 
+// 32-window groups per lane in a warp tile of the per-pattern scan kernel of
+// variant v (resolved) at this k: 8 for the window-sliced kernel with k = 0,
+// whose evaluation per tile is short enough that the per-tile work (copies,
+// list reads, early-stop checks) weighs, else 4.  A tile covers
+// 1024 * scan_groups windows.
+inline int scan_groups(Variant v, int32_t k) { return v == Variant::kWindowSliced && k == 0 ? 8 : 4; }
+inline uint64_t scan_tile_windows(Variant v, int32_t k) { return 1024ull * (uint64_t)scan_groups(v, k); }
+
 // PM_VARIANT_* (not AUTO) <-> Variant.
 inline Variant variant_from_public(int32_t v)
 {
@@ -210,7 +220,43 @@ inline void desc_constants(PatDesc &d)
 {
     d.two = 2u;
     d.variant = 0u;
-    d.pad0 = 0u;
+    d.c0 = 0u;
+}
+
+// The chunk a pattern-sliced scan tests first: Eq. 4's sum does not depend on
+// the order of its terms, so the first stage may take any 32 (or, C = 2, 64)
+// consecutive positions, and the fewer windows pass it the fewer need
+// settling.  Chosen among the full chunks (C consecutive ones) as the one
+// with the fewest expected matches under the text's letter frequencies
+// (each position contributes the share of the text held by its class's
+// letters); chunk 0 unless another one expects at least a tenth of a match
+// less.  The settling counts chunks c0 and c0+1 from the staged tile first,
+// so the others are read only for the rare windows that survive both.
+inline uint32_t first_stage_chunk(const pm_pattern *p, const pm_text *t, int C)
+{
+    const uint32_t full = p->m / 32;
+    if (full < (uint32_t)C + 1) return 0u;
+    const double tot = (double)(t->count[0] + t->count[1] + t->count[2] + t->count[3]);
+    if (tot <= 0) return 0u;
+    double f[4];
+    for (int a = 0; a < 4; ++a) f[a] = (double)t->count[a] / tot;
+    auto expect = [&](uint32_t c) {
+        const uint4 w = p->masks[c];
+        return f[0] * __builtin_popcount(w.x) + f[1] * __builtin_popcount(w.y) +
+               f[2] * __builtin_popcount(w.z) + f[3] * __builtin_popcount(w.w);
+    };
+    double best = 0.0, e0 = 0.0;
+    uint32_t arg = 0;
+    for (uint32_t c = 0; c + (uint32_t)C <= full; ++c) {
+        double e = expect(c);
+        if (C == 2) e += expect(c + 1);
+        if (c == 0) e0 = best = e;
+        else if (e < best) {
+            best = e;
+            arg = c;
+        }
+    }
+    return best <= e0 - 0.1 ? arg : 0u;
 }
 
 // A (pattern, tile) segment of hits left by the batched scan: key =

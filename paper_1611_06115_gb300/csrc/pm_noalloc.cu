@@ -112,6 +112,7 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
 
     // descriptors; a handle repeated with several k is packed once
     PatDesc desc[kNaMaxPatterns];
+    Variant var[kNaMaxPatterns];
     uint64_t tile0[kNaMaxPatterns + 1];
     const pm_pattern *distinct[kNaMaxPatterns];
     uint64_t where[kNaMaxPatterns];
@@ -138,8 +139,13 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
         d.masks = mo;
         d.wslist = mo + pt->nchunks;
         d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
+        const Variant v = auto_variant(d, dev);
+        var[p] = v;
+        if (v == Variant::kPatternSliced || v == Variant::kPatternSliced2)
+            d.c0 = first_stage_chunk(pt, text, v == Variant::kPatternSliced2 ? 2 : 1);
+        const uint64_t tw = scan_tile_windows(v, d.k);
         d.tile0 = entries;
-        d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
+        d.ntiles = (d.nwin + tw - 1) / tw;
         entries += d.ntiles;
         tile0[p] = d.tile0;
     }
@@ -189,7 +195,7 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
     // status word must start at zero (the tile table is rewritten in full)
     if (!rc) rc = cuda_status(cudaMemsetAsync(ctl, 0, 256, st), "clear control words");
     for (uint32_t p = 0; !rc && p < npat; ++p) {
-        const Variant v = auto_variant(desc[p], dev);
+        const Variant v = var[p];
         rc = cuda_status(launch_scan(v, text->planes, text->unk, desc[p], d_masks, d_table, d_tmp, capacity,
                                      d_cursor, d_status, scan_grid_limit(v, desc[p].k, dev), st),
                          "scan kernel");

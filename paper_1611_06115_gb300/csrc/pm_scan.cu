@@ -60,15 +60,16 @@ using namespace scan;
 // 0..kWsMaxK window-sliced with threshold K.  The -2 kernel keeps 32 running
 // counts per lane in registers, so it takes twice the registers at half the
 // resident warps; the window-sliced kernels with K >= 3 keep K+1 counter
-// words per group and run three CTAs per SM.
+// words per group, the one with K = 0 eight groups per lane (tiles of 8192
+// windows, scan_groups), and run three CTAs per SM.
 //
 // Each warp stages its tiles kStages strides ahead, one commit group of
 // asynchronous copies per tile (an empty group once the tiles run out, so
 // that group i always belongs to the warp's i-th tile); a stage is refilled
 // once its tile is done (settling and hit counts read the staged tile).
 // Tile indices fit in 32 bits: a text has fewer than 2^32 symbols.
-template <int VARIANT>
-__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 3 ? 3 : 4))
+template <int VARIANT, int G>
+__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 3 || G == 8 ? 3 : 4))
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status,
@@ -77,14 +78,16 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
     constexpr bool kWS = VARIANT >= 0;
     constexpr uint32_t S = kStages;
 
-    __shared__ __align__(128) uint2 sbuf[kScanWarps][S][kStageBlocks];
+    __shared__ __align__(128) uint2 sbuf[kScanWarps][S][scan_stage_blocks<G>()];
     __shared__ uint4 slist[kWS ? 64 : 1];
     __shared__ uint32_t squeue[kScanWarps][kQueueCap];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint4 *__restrict__ M = arena + d.masks;
-    const uint4 M0 = __ldg(M);
+    const uint4 M0 = __ldg(M + d.c0);
+    // stages start at the even block at or below block tile*32G + c0 (16-byte copies)
+    const uint32_t c0e = d.c0 & ~1u, sh = d.c0 & 1u;
     const PsConst pc = ps_const(d.two, (uint32_t)d.k);
 
     if (kWS) {
@@ -93,12 +96,14 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
         __syncthreads();  // the only CTA-wide barrier: the list is shared by all warps
     }
     const uint32_t ntiles = (uint32_t)d.ntiles;
-    const uint32_t nfull = (uint32_t)(d.nwin / kTileWindows);  // tiles whose windows are all valid
+    const uint32_t nfull = (uint32_t)(d.nwin / (1024u * G));  // tiles whose windows are all valid
     const uint32_t stride = gridDim.x * kScanWarps;
     const uint32_t first = blockIdx.x * kScanWarps + warp;
 #pragma unroll
     for (uint32_t st = 0; st < S; ++st) {
-        if (first + st * stride < ntiles) copy_tile_async(planes, first + st * stride, &sbuf[warp][st][0], lane);
+        if (first + st * stride < ntiles)
+            copy_tile_async<G>(planes, (uint64_t)(first + st * stride) * (32u * G) + c0e, &sbuf[warp][st][0],
+                               lane);
         cp_async_commit();
     }
 
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
     for (uint32_t tile = first; tile < ntiles; tile += stride) {
         cp_async_wait<S - 1>();  // this tile's group has landed (later ones may be pending)
         __syncwarp();            // ... for every lane's pieces
-        const uint2 *stage = &sbuf[warp][s][0];
+        const uint2 *stage = &sbuf[warp][s][sh];  // block tile*32G + c0
         uint2 a[G], b[G];
         uint32_t valid[G], pass[G];
 #pragma unroll
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
 #pragma unroll
             for (int g = 0; g < G; ++g) valid[g] = valid_mask((uint64_t)tile * (32u * G) + 32u * g + lane, d.nwin);
         }
-        const bool need = tile_first_stage<VARIANT>(a, b, tile, valid, d, M, M0, slist, pc, planes, stage, pass);
+        const bool need = tile_first_stage<VARIANT, G>(a, b, tile, valid, d, M, M0, slist, pc, planes, stage, pass);
 
         // ---- exact counts and hits of this warp tile, in window order ----
         uint32_t anyp = 0;
@@ -129,20 +134,21 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
         for (int g = 0; g < G; ++g) anyp |= pass[g];
         TileEntry *entry = table + d.tile0 + tile;
         if (__any_sync(kFull, anyp != 0u)) {
-            if (!settle_emit_queued(pass, tile, stage, squeue[warp], d, M, planes, unk, tmp, cap, cursor,
-                                    entry)) {
+            if (!settle_emit_queued<G>(pass, tile, stage, squeue[warp], d, M, planes, unk, tmp, cap, cursor,
+                                       entry)) {
                 // more candidates than the queue holds (dense hits): each lane its own
                 uint64_t blk[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) blk[g] = (uint64_t)tile * (32u * G) + 32u * g + lane;
-                settle_dense<VARIANT>(need, a, b, blk, d, M, planes, stage, pass);
+                settle_dense<VARIANT, G>(need, a, b, blk, d, M, planes, stage, pass);
                 anyp = 0;
 #pragma unroll
                 for (int g = 0; g < G; ++g) anyp |= pass[g];
                 if (__any_sync(kFull, anyp != 0u)) {
                     uint32_t total;
                     unsigned long long base;
-                    emit_tile_hits<true>(pass, blk, a, b, M0, d, M, planes, unk, tmp, cap, cursor, total, base);
+                    emit_tile_hits<true, G>(pass, blk, a, b, stage, d, M, planes, unk, tmp, cap, cursor, total,
+                                            base);
                     if (lane == 0) *entry = TileEntry{total, (uint32_t)base};
                 } else if (lane == 0) {
                     *entry = TileEntry{0u, 0u};
@@ -153,36 +159,37 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
         }
         // refill this stage with the tile S strides ahead
         __syncwarp();  // every lane is done reading the stage
-        if (tile + S * stride < ntiles) copy_tile_async(planes, tile + S * stride, &sbuf[warp][s][0], lane);
+        if (tile + S * stride < ntiles)
+            copy_tile_async<G>(planes, (uint64_t)(tile + S * stride) * (32u * G) + c0e, &sbuf[warp][s][0], lane);
         cp_async_commit();
         if (++s == S) s = 0;
     }
     cp_async_wait<0>();  // nothing in flight when the warp leaves
 }
 
-template <int VARIANT>
+template <int VARIANT, int G>
 const void *kernel_ptr()
 {
-    return (const void *)&k_scan<VARIANT>;
+    return (const void *)&k_scan<VARIANT, G>;
 }
 
-// v already resolved for k
+// v already resolved for k; the tile width as scan_groups(v, k)
 const void *select_kernel(Variant v, int32_t k)
 {
     switch (v) {
     case Variant::kWindowSliced:
         switch (k) {
-        case 0: return kernel_ptr<0>();
-        case 1: return kernel_ptr<1>();
-        case 2: return kernel_ptr<2>();
-        case 3: return kernel_ptr<3>();
-        case 4: return kernel_ptr<4>();
-        case 5: return kernel_ptr<5>();
-        default: return kernel_ptr<6>();
+        case 0: return kernel_ptr<0, 8>();
+        case 1: return kernel_ptr<1, 4>();
+        case 2: return kernel_ptr<2, 4>();
+        case 3: return kernel_ptr<3, 4>();
+        case 4: return kernel_ptr<4, 4>();
+        case 5: return kernel_ptr<5, 4>();
+        default: return kernel_ptr<6, 4>();
         }
-    case Variant::kPatternSliced: return kernel_ptr<-1>();
-    case Variant::kPatternSliced2: return kernel_ptr<-3>();
-    default: return kernel_ptr<-2>();
+    case Variant::kPatternSliced: return kernel_ptr<-1, 4>();
+    case Variant::kPatternSliced2: return kernel_ptr<-3, 4>();
+    default: return kernel_ptr<-2, 4>();
     }
 }
 

@@ -10,7 +10,8 @@ namespace scan {
 using dev::class_match;
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr int G = kGroups;
+constexpr int G = kGroups;  // groups per warp tile of the batched kernel; the per-pattern
+                            // kernels take theirs as a template parameter
 
 // Mismatch count of window 32*blk + w over chunks c0.., starting from
 // `count`, stopping once it exceeds `limit` (then some value > limit).
@@ -165,7 +166,7 @@ __device__ __forceinline__ void add_position(uint32_t (&L)[K + 1], uint32_t matc
 }
 
 // True when every window of the lane's groups, on every lane, is past K.
-template <int K>
+template <int K, int G>
 __device__ __forceinline__ bool all_past(const uint32_t (&L)[G][K + 1])
 {
     uint32_t d = kFull;
@@ -186,7 +187,7 @@ constexpr int kWsCut = 2;   // `cut` entries tested, some window alive
 // into one update.  The early stop is checked whenever e reaches a multiple
 // of the block size S (2 entries for K = 0 from entry 4 on, else 4), across
 // run boundaries, as if the list were one run.
-template <int K, int CODE, bool kGlobal>
+template <int K, int CODE, bool kGlobal, int G>
 __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&b)[G],
                                              const uint4 *__restrict__ list, uint32_t &e,
                                              uint32_t end, uint32_t cut, uint32_t (&L)[G][K + 1])
@@ -200,7 +201,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
     constexpr uint32_t S = K == 0 ? 2u : 4u;
     auto check = [&]() -> int {
         if (K == 0 && e < 4) return kWsGoOn;
-        if (all_past<K>(L)) return kWsDead;
+        if (all_past<K, G>(L)) return kWsDead;
         if (e >= cut) return kWsCut;
         return kWsGoOn;
     };
@@ -253,7 +254,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
 // cheaper to count one by one than to carry the whole tile through the
 // remaining positions.  Returns false when every listed position was tested
 // (alive is then exact over the first 32 positions) or every window died.
-template <int K, bool kGlobal = false>
+template <int K, bool kGlobal = false, int G>
 __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
                                                     const uint4 *__restrict__ list,
                                                     uint32_t n_single, uint32_t n_general,
@@ -273,10 +274,10 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
         const uint32_t end = h.z > e ? (h.z < n_single ? h.z : n_single) : e + 1;
         int r;
         switch (h.y & 3u) {
-        case 0: r = ws_letter_run<K, 0, kGlobal>(a, b, list, e, end, cut, L); break;
-        case 1: r = ws_letter_run<K, 1, kGlobal>(a, b, list, e, end, cut, L); break;
-        case 2: r = ws_letter_run<K, 2, kGlobal>(a, b, list, e, end, cut, L); break;
-        default: r = ws_letter_run<K, 3, kGlobal>(a, b, list, e, end, cut, L); break;
+        case 0: r = ws_letter_run<K, 0, kGlobal, G>(a, b, list, e, end, cut, L); break;
+        case 1: r = ws_letter_run<K, 1, kGlobal, G>(a, b, list, e, end, cut, L); break;
+        case 2: r = ws_letter_run<K, 2, kGlobal, G>(a, b, list, e, end, cut, L); break;
+        default: r = ws_letter_run<K, 3, kGlobal, G>(a, b, list, e, end, cut, L); break;
         }
         if (r != kWsGoOn) {
 #pragma unroll
@@ -294,7 +295,7 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
             add_position<K>(L[g], class_match(lo, hi, M));
         }
         if ((c & 3) == 3) {
-            if (all_past<K>(L)) {
+            if (all_past<K, G>(L)) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) alive[g] = 0u;
                 return false;
@@ -319,24 +320,33 @@ __device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, u
     dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
 }
 
-// One warp tile and its halo, global -> shared, by the warp's own lanes:
-// 16-byte asynchronous copies (cp.async), lane l taking pieces l and l + 32
-// and lane 0 the halo piece, as one commit group per lane.  Both addresses
-// are 16-byte aligned (tiles start at multiples of 1024 bytes).  Complete
-// once every lane has passed cp_async_wait for the group and the warp has
-// synchronised.
-static_assert(kStageBytes == 32 * 2 * 16 + 16, "a warp tile is 64 pieces of 16 bytes plus the halo");
-__device__ __forceinline__ void copy_tile_async(const uint2 *planes, uint32_t tile, uint2 *dst, int lane)
+// Blocks a per-pattern scan stage holds: a warp tile of 32G blocks from an
+// even block (the one at or below the tile's first block plus the first-stage
+// chunk), the 2-block halo, and one more block so that the count is even.
+template <int G>
+__host__ __device__ constexpr uint32_t scan_stage_blocks() { return 32u * G + 4u; }
+
+// One stage for the per-pattern scan, global -> shared, by the warp's own
+// lanes: scan_stage_blocks<G>() blocks from block `first` (even, so that both
+// addresses are 16-byte aligned) as 16-byte asynchronous copies (cp.async),
+// lane l taking pieces l, l + 32, ... and lanes 0 and 1 the last two, as one
+// commit group per lane.  Complete once every lane has passed cp_async_wait
+// for the group and the warp has synchronised.
+template <int G>
+__device__ __forceinline__ void copy_tile_async(const uint2 *planes, uint64_t first, uint2 *dst, int lane)
 {
-    const char *src = (const char *)(planes + (uint64_t)tile * (32u * G));
+    constexpr uint32_t kPieces = scan_stage_blocks<G>() / 2;  // 16 bytes each
+    static_assert(kPieces == 16 * G + 2, "32 lanes take 16G pieces, lanes 0 and 1 the last two");
+    const char *src = (const char *)(planes + first);
     const uint32_t d = dev::smem_u32(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * lane), "l"(src + 16 * lane)
-                 : "memory");
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * (lane + 32)),
-                 "l"(src + 16 * (lane + 32))
-                 : "memory");
-    if (lane == 0)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 1024u), "l"(src + 1024)
+#pragma unroll
+    for (uint32_t i = 0; i < 16u * G; i += 32u)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * (i + lane)),
+                     "l"(src + 16 * (i + lane))
+                     : "memory");
+    if (lane < 2)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * (16u * G + lane)),
+                     "l"(src + 16 * (16 * G + lane))
                      : "memory");
 }
 
@@ -405,27 +415,45 @@ __device__ __forceinline__ uint32_t settle_lane(uint32_t pass, uint64_t blk,
     return pass;
 }
 
-// settle_lane for a lane whose blocks blk and blk+1 are in registers (t0, t1)
-// and whose block blk+2 is still staged in shared memory (s_next): chunks 0
-// and 1 need no load through L1/L2, deeper chunks (rarely reached while k is
-// below the expected mismatches of 64 positions) use window_count_from.
+// The count of window 32*blk + w, exact up to k (once past k, some value
+// above k), when blocks blk+c0 and blk+c0+1 are at hand (t0, t1) and block
+// blk+c0+2 is still staged at *s_t2: chunks c0 and c0+1 from those, the
+// others through L1/L2 (rarely reached while k is below the expected
+// mismatches of 64 positions).
+__device__ __forceinline__ uint32_t count_from_first(uint2 t0, uint2 t1, const uint2 *s_t2, uint64_t blk,
+                                                     uint32_t w, const uint4 *__restrict__ M, uint32_t c0,
+                                                     uint32_t nchunks, uint32_t k,
+                                                     const uint2 *__restrict__ planes)
+{
+    uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), __ldg(M + c0)));
+    if (c > k) return c;
+    if (c0 + 1 < nchunks) {
+        const uint2 t2 = *s_t2;
+        c += __popc(~class_match(__funnelshift_r(t1.x, t2.x, w), __funnelshift_r(t1.y, t2.y, w),
+                                 __ldg(M + c0 + 1)));
+        if (c > k) return c;
+    }
+    if (c0 > 0) {
+        c = window_count_from(planes, blk, w, M, 0, c0, c, k);
+        if (c > k) return c;
+    }
+    if (c0 + 2 < nchunks) c = window_count_from(planes, blk, w, M, c0 + 2, nchunks, c, k);
+    return c;
+}
+
+// Exact counts of the windows still in `pass` for a lane whose blocks
+// blk+c0 and blk+c0+1 are in registers (t0, t1) and whose block blk+c0+2 is
+// still staged in shared memory (s_next): drops those past k.
 __device__ __forceinline__ uint32_t settle_staged(uint32_t pass, uint64_t blk, uint2 t0, uint2 t1,
                                                  const uint2 *s_next, const uint4 *__restrict__ M,
-                                                 uint32_t nchunks, uint32_t k,
+                                                 uint32_t c0, uint32_t nchunks, uint32_t k,
                                                  const uint2 *__restrict__ planes)
 {
-    if (!pass) return 0u;
-    const uint4 M0 = __ldg(M), M1 = __ldg(M + 1);
-    const uint2 t2 = *s_next;
     uint32_t sv = pass;
     while (sv) {
         const uint32_t w = __ffs(sv) - 1;
         sv &= sv - 1;
-        uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), M0));
-        if (c <= k)
-            c += __popc(~class_match(__funnelshift_r(t1.x, t2.x, w), __funnelshift_r(t1.y, t2.y, w), M1));
-        if (c <= k && nchunks > 2) c = window_count_from(planes, blk, w, M, 2, nchunks, c, k);
-        if (c > k) pass &= ~(1u << w);
+        if (count_from_first(t0, t1, s_next, blk, w, M, c0, nchunks, k, planes) > k) pass &= ~(1u << w);
     }
     return pass;
 }
@@ -470,10 +498,13 @@ __device__ __forceinline__ PsConst ps_const(uint32_t two, uint32_t k)
 // First stage of one warp tile: pass[g] bit w for window 32*blk[g] + w,
 // a superset of the windows of the tile that hold the pattern with at most k
 // mismatches (VARIANT as in k_scan; list is the window-sliced position list
-// in shared memory; stage the tile still staged in shared memory).  Returns
+// in shared memory; stage the tile still staged in shared memory, from
+// block tile*32G + d.c0 on; a[g], b[g] its blocks 32g + lane and 32g + lane
+// + 1; M0 the masks of chunk d.c0, which the pattern-sliced evaluations test
+// first, the others chunk 0).  Returns
 // true when pass still needs exact counts past the positions tested (see
 // settle_dense or settle_emit_queued); false when pass is exact.
-template <int VARIANT>
+template <int VARIANT, int G>
 __device__ __forceinline__ bool tile_first_stage(const uint2 (&a)[G], const uint2 (&b)[G],
                                                  uint32_t tile, const uint32_t (&valid)[G],
                                                  const PatDesc &d, const uint4 *__restrict__ M,
@@ -499,7 +530,8 @@ __device__ __forceinline__ bool tile_first_stage(const uint2 (&a)[G], const uint
         // reads as all ones: every position past m matches)
         constexpr int C = VARIANT == -3 ? 2 : 1;
         const int lane = threadIdx.x & 31;
-        const uint4 M1 = (C == 2 && d.nchunks > 1) ? __ldg(M + 1) : make_uint4(kFull, kFull, kFull, kFull);
+        const uint4 M1 = (C == 2 && d.c0 + 1 < d.nchunks) ? __ldg(M + d.c0 + 1)
+                                                           : make_uint4(kFull, kFull, kFull, kFull);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             uint32_t t = 0u;
@@ -510,13 +542,13 @@ __device__ __forceinline__ bool tile_first_stage(const uint2 (&a)[G], const uint
             }
             pass[g] = t;
         }
-        return d.nchunks > (uint32_t)C;
+        return d.nchunks > (uint32_t)C;  // (c0 > 0 only when nchunks > C)
     }
 }
 
 // Exact counts for pass (when `need`), each lane settling its own windows:
 // the path for tiles with more candidates than settle_emit_queued takes.
-template <int VARIANT>
+template <int VARIANT, int G>
 __device__ __forceinline__ void settle_dense(bool need, const uint2 (&a)[G], const uint2 (&b)[G],
                                              const uint64_t (&blk)[G], const PatDesc &d,
                                              const uint4 *__restrict__ M,
@@ -531,8 +563,8 @@ __device__ __forceinline__ void settle_dense(bool need, const uint2 (&a)[G], con
         if constexpr (VARIANT >= 0)
             pass[g] = settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, k, planes);
         else if constexpr (VARIANT == -1 || VARIANT == -3)
-            pass[g] = settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M, d.nchunks,
-                                    k, planes);
+            pass[g] = settle_staged(pass[g], blk[g], a[g], b[g], stage + 32 * g + lane + 2, M, d.c0,
+                                    d.nchunks, k, planes);
         else
             pass[g] = settle_lane(pass[g], blk[g], M, d.nchunks, k, planes);
     }
@@ -542,15 +574,15 @@ __device__ __forceinline__ void settle_dense(bool need, const uint2 (&a)[G], con
 // warp-aggregated atomic on cursor.  Call with the whole warp and only when
 // some lane has a pass bit.  Returns (on every lane) the number of hits and
 // where they start in tmp.
-// kRegs: the lane's blocks a[g], b[g] (registers) and the chunk-0 masks M0
-// give the first 32 positions of a hit's count without a memory access
-// (deeper chunks, and texts with unknown symbols, count through L1/L2); used
-// by the pattern-sliced kernels, whose hits are dense for small m and large
-// k.  Otherwise every hit is counted through L1/L2, which keeps a and b out
-// of registers during emission.
-template <bool kRegs>
+// kRegs: the lane's blocks a[g], b[g] (registers, blocks blk+c0 and
+// blk+c0+1) and the still-staged tile (stage, from block tile*32G + d.c0 on)
+// give chunks c0 and c0+1 of a hit's count without a load through L1/L2
+// (other chunks, and texts with unknown symbols, count through L1/L2); hits
+// are dense for small m and large k.  Otherwise every hit is counted through
+// L1/L2, which keeps a and b out of registers during emission.
+template <bool kRegs, int G>
 __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64_t (&blk)[G],
-                                               const uint2 (&a)[G], const uint2 (&b)[G], uint4 M0,
+                                               const uint2 (&a)[G], const uint2 (&b)[G], const uint2 *stage,
                                                const PatDesc &d, const uint4 *__restrict__ M,
                                                const uint2 *__restrict__ planes,
                                                const uint32_t *__restrict__ unk,
@@ -594,10 +626,8 @@ __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64
                 if (!kRegs || unk) {
                     c = window_count_exact(planes, unk, blk[g], w, M, d.nchunks, (uint32_t)d.k);
                 } else {
-                    c = __popc(~class_match(__funnelshift_r(a[g].x, b[g].x, w),
-                                            __funnelshift_r(a[g].y, b[g].y, w), M0));
-                    if (d.nchunks > 1)
-                        c = window_count_from(planes, blk[g], w, M, 1, d.nchunks, c, (uint32_t)d.k);
+                    c = count_from_first(a[g], b[g], stage + 32 * g + lane + 2, blk[g], w, M, d.c0, d.nchunks,
+                                         (uint32_t)d.k, planes);
                 }
                 tmp[q] = pm_hit{(uint32_t)(blk[g] * 32ull + w), c};
             }
@@ -612,43 +642,31 @@ __device__ __forceinline__ void emit_tile_hits(uint32_t (&pass)[G], const uint64
 constexpr uint32_t kQueueCap = 256;
 
 // The count of window 32*blk + w, exact up to k (once past k, some value
-// above k).  kStaged: blocks blk .. blk+2 are still staged in shared memory
-// at stage_blk[0..2], so the first two chunks need no load through L1/L2.
-template <bool kStaged>
+// above k), whose blocks blk+c0 .. blk+c0+2 are staged at stage_blk[0..2].
 __device__ __forceinline__ uint32_t candidate_count(const uint2 *stage_blk, uint64_t blk, uint32_t w,
-                                                    const uint4 *__restrict__ M, uint32_t nchunks,
-                                                    uint32_t k, const uint2 *__restrict__ planes,
+                                                    const uint4 *__restrict__ M, uint32_t c0,
+                                                    uint32_t nchunks, uint32_t k,
+                                                    const uint2 *__restrict__ planes,
                                                     const uint32_t *__restrict__ unk)
 {
     if (unk) return window_count_exact(planes, unk, blk, w, M, nchunks, k);
-    if constexpr (kStaged) {
-        const uint2 t0 = stage_blk[0], t1 = stage_blk[1];
-        uint32_t c = __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), __ldg(M)));
-        if (c <= k && nchunks > 1) {
-            const uint2 t2 = stage_blk[2];
-            c += __popc(~class_match(__funnelshift_r(t1.x, t2.x, w), __funnelshift_r(t1.y, t2.y, w),
-                                     __ldg(M + 1)));
-            if (c <= k && nchunks > 2) c = window_count_from(planes, blk, w, M, 2, nchunks, c, k);
-        }
-        return c;
-    } else {
-        return window_count_from(planes, blk, w, M, 0, nchunks, 0u, k);
-    }
+    return count_from_first(stage_blk[0], stage_blk[1], stage_blk + 2, blk, w, M, c0, nchunks, k, planes);
 }
 
 // Settle and emit the candidates of one warp tile (cand[g] bit w: window
-// 32*(tile*32G + 32g + lane) + w; the tile still staged at `stage`) with the
-// whole warp working on them together, whichever lanes they came from: the
-// candidates are written, in
-// window order, to the warp's queue q in shared memory (kQueueCap entries);
-// each lane then counts every 32nd of them exactly (up to k), the hits are
+// 32*(tile*32G + 32g + lane) + w; the tile still staged at `stage`, from
+// block tile*32G + d.c0 on) with the whole warp working on them together,
+// whichever lanes they came from: the candidates are written, in window
+// order, to the warp's queue q in shared memory (kQueueCap entries); each
+// lane then counts every 32nd of them exactly (up to k), the hits are
 // compacted in place, in window order, and written once to tmp behind one
 // warp-aggregated atomic on cursor (coalesced); *entry receives {hits,
 // first}.  A lane that held candidates in one group of a tile would
 // otherwise keep the other 31 lanes waiting while it counts them one by one.
 // Returns false, having done nothing, when the tile has more than kQueueCap
-// candidates or k >= 2^20 (a count is packed with its window in 32 bits).
-// Call with the whole warp.
+// candidates or k is too large for a count to share 32 bits with its
+// window.  Call with the whole warp.
+template <int G>
 __device__ __forceinline__ bool settle_emit_queued(const uint32_t (&cand)[G], uint32_t tile,
                                                    const uint2 *stage, uint32_t *q, const PatDesc &d,
                                                    const uint4 *__restrict__ M,
@@ -658,30 +676,44 @@ __device__ __forceinline__ bool settle_emit_queued(const uint32_t (&cand)[G], ui
                                                    unsigned long long *__restrict__ cursor,
                                                    TileEntry *entry)
 {
-    static_assert(G == 4, "one byte per group");
+    static_assert(G == 4 || G == 8, "one byte per group, four groups per word");
+    constexpr int NW = G / 4;                        // words of packed group counts
+    constexpr uint32_t kWinBits = G == 4 ? 12u : 13u;  // window within the tile
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t k = (uint32_t)d.k;
-    // byte g: this lane's candidates in group g (at most 32 each)
-    uint32_t packed = 0;
+    // byte j of word i: this lane's candidates in group 4i + j (at most 32 each)
+    uint32_t packed[NW];
+    uint32_t mine = 0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) packed |= (uint32_t)__popc(cand[g]) << (8 * g);
-    const uint32_t total = __reduce_add_sync(kFull, (packed * 0x01010101u) >> 24);
-    if (total > kQueueCap || k >= (1u << 20)) return false;
-    // Inclusive scan over the lanes of all four bytes at once: no byte ever
-    // exceeds total <= 255, so bytes never carry into each other.
-    uint32_t incl = packed;
+    for (int i = 0; i < NW; ++i) {
+        packed[i] = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (uint32_t)o) incl += v;
+        for (int j = 0; j < 4; ++j) packed[i] |= (uint32_t)__popc(cand[4 * i + j]) << (8 * j);
+        mine += (packed[i] * 0x01010101u) >> 24;  // sum of the bytes (at most 128)
     }
-    const uint32_t tot = __shfl_sync(kFull, incl, 31);
-    // byte g: where this lane's group-g candidates start (all of groups < g,
-    // then those of group g on the lanes before this one)
-    const uint32_t pos = tot * 0x01010100u + (incl - packed);
+    const uint32_t total = __reduce_add_sync(kFull, mine);
+    if (total > kQueueCap || k >= (1u << (32u - kWinBits))) return false;
+    // Inclusive scans over the lanes of four bytes at once: no byte ever
+    // exceeds total <= 255, so bytes never carry into each other.
+    uint32_t pos[NW];
+    uint32_t before = 0;  // candidates of the groups of earlier words
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        uint32_t incl = packed[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (uint32_t)o) incl += v;
+        }
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        // byte j: where this lane's candidates of group 4i + j start (all of
+        // the earlier groups, then those of this group on earlier lanes)
+        pos[i] = before * 0x01010101u + tot * 0x01010100u + (incl - packed[i]);
+        before += (tot * 0x01010101u) >> 24;
+    }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        uint32_t p = (pos >> (8 * g)) & 0xffu;
+        uint32_t p = (pos[g / 4] >> (8 * (g % 4))) & 0xffu;
         uint32_t m = cand[g];
         while (m) {
             const uint32_t w = __ffs(m) - 1;
@@ -698,10 +730,10 @@ __device__ __forceinline__ bool settle_emit_queued(const uint32_t (&cand)[G], ui
         if (i < total) {
             const uint32_t e = q[i];
             const uint32_t gl = e >> 5;  // block within the tile
-            const uint32_t c = candidate_count<true>(stage + gl, (uint64_t)tile * (32u * G) + gl, e & 31u, M,
-                                                     d.nchunks, k, planes, unk);
+            const uint32_t c = candidate_count(stage + gl, (uint64_t)tile * (32u * G) + gl, e & 31u, M, d.c0,
+                                               d.nchunks, k, planes, unk);
             hit = c <= k;
-            rec = e | (c << 12);
+            rec = e | (c << kWinBits);
         }
         const uint32_t hb = __ballot_sync(kFull, hit);
         __syncwarp();  // every entry of this round is read before any is overwritten
@@ -713,10 +745,11 @@ __device__ __forceinline__ bool settle_emit_queued(const uint32_t (&cand)[G], ui
         __syncwarp();
         if (lane == 0) base = atomicAdd(cursor, (unsigned long long)hits);
         base = __shfl_sync(kFull, base, 0);
-        const uint64_t w0 = (uint64_t)tile * kTileWindows;
+        const uint64_t w0 = (uint64_t)tile * (1024u * G);
         for (uint32_t i = lane; i < hits; i += 32) {
             const uint32_t r = q[i];
-            if (base + i < cap) tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & 4095u)), r >> 12};
+            if (base + i < cap)
+                tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & ((1u << kWinBits) - 1u))), r >> kWinBits};
         }
     }
     if (lane == 0) *entry = TileEntry{hits, (uint32_t)base};

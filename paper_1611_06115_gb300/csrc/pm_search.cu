@@ -197,6 +197,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
 
     // ---- descriptors and the arena (chunk masks, window-sliced lists) ----
     std::vector<PatDesc> desc(npat);
+    std::vector<Variant> var(npat);
     struct Placed { uint64_t masks, list; };
     std::unordered_map<const pm_pattern *, Placed> where;
     uint64_t nmask = 0, entries = 0;
@@ -218,8 +219,14 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
         d.masks = it->second.masks;
         d.wslist = it->second.list;
         d.nwin = pt->m <= text->n ? text->n - pt->m + 1 : 0;
+        const Variant v = o.variant == PM_VARIANT_AUTO ? auto_variant(d, dev)
+                                                       : resolve_variant(variant_from_public(o.variant), d.k);
+        var[p] = v;
+        if (v == Variant::kPatternSliced || v == Variant::kPatternSliced2)
+            d.c0 = first_stage_chunk(pt, text, v == Variant::kPatternSliced2 ? 2 : 1);
+        const uint64_t tw = scan_tile_windows(v, d.k);
         d.tile0 = entries;
-        d.ntiles = (d.nwin + kTileWindows - 1) / kTileWindows;
+        d.ntiles = (d.nwin + tw - 1) / tw;
         entries += d.ntiles;
     }
 
@@ -280,9 +287,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
 
     // ---- one scan launch per pattern ----
     for (uint32_t p = 0; !rc && p < npat; ++p) {
-        const Variant v = o.variant == PM_VARIANT_AUTO
-                              ? auto_variant(desc[p], dev)
-                              : resolve_variant(variant_from_public(o.variant), desc[p].k);
+        const Variant v = var[p];
         const int grid = o.grid > 0 ? o.grid : scan_grid_limit(v, desc[p].k, dev);
         if (o.events) cudaEventRecord((cudaEvent_t)o.events[2 * p], st);
         rc = cuda_status(launch_scan(v, text->planes, text->unk, desc[p], d_masks, d_table, d_tmp, capacity,
