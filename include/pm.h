@@ -282,9 +282,9 @@ pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
  * Batched search: many (pattern, k) pairs of uneven m and k in ONE
  * persistent kernel launch over the resident text (Eq. 4 with the early
  * stop of Sec. 2.4-2.5, tiles with m-1 overlap as in Sec. 2.6).  Each text
- * tile is staged once and every pattern of a group runs over it, so the
- * text is read from device memory about once for the whole batch.  Results
- * are identical to pm_search's for the same pairs.
+ * tile is staged once for every pattern of a work item's row, so the text is
+ * read from device memory once per row (by default one row per kind of
+ * evaluation).  Results are identical to pm_search's for the same pairs.
  *
  * pm_batch_create  copies the patterns' compiled data and k to the device
  *                  and allocates all scratch for up to `capacity` hits
@@ -292,8 +292,9 @@ pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
  *                  pattern handles may be freed afterwards; the text must
  *                  outlive the batch.  Waits for its uploads.
  * options          NULL for defaults, or (0 in any field: its default):
- *                    group      pairs per work item, rounded up to a
- *                               multiple of 8 (default 16);
+ *                    group      pairs per work item row, rounded up to a
+ *                               multiple of 8 (default: every pair of the
+ *                               row's kind);
  *                    grid       CTAs of the persistent launch (default: as
  *                               many as the device keeps resident);
  *                    tiles      warp tiles of 4096 windows per work item,

@@ -4,24 +4,27 @@
 // The planner sorts the (pattern, k) pairs into categories by evaluation
 // (window-sliced per k, pattern-sliced over 32 positions, over 64 positions,
 // every chunk; thresholds are options), orders each category by m and cuts
-// it into groups of kP pairs and rows of groups.  A work item is a row
-// crossed with a run of warp tiles; rows are outermost, so all warps run one
-// kind of evaluation at a time and the text is read from device memory
-// about once per row.  A warp stages its tiles (plus halo) in shared memory
-// by bulk copies two tiles ahead, then per group of the row
+// it into groups of kP pairs; a row holds the groups of one category (all
+// of them unless the options cut it shorter).  A work item is a row crossed
+// with a run of warp tiles; rows are outermost, so all warps run one kind of
+// evaluation at a time, and each tile is staged once for every pair of its
+// row: the text is read from device memory once per row.  A warp stages its
+// tiles (plus halo) in shared memory by its lanes' own asynchronous copies
+// kStages tiles ahead, then per group of the row
 //   * pattern-sliced group: for each window, the funnel shifts that line the
 //     text up with the first 32 (or 64) positions are done once and serve
 //     every pair of the group (whose masks sit in shared memory), so a
 //     pair-window costs three (or six) selects, one (or two) popcounts and a
 //     quarter of the byte-packed threshold test;
-//   * window-sliced group: each pair runs the thermometer-counter scan over
-//     the tile, reading its position list through the read-only path;
+//   * window-sliced group: each pair copies its position list to shared
+//     memory and runs the letter-plane thermometer scan over the tile;
 //   * every-chunk group: each pair keeps 32 running counts per lane.
-// Every 1024-window group of a tile with hits for a pair writes them
-// contiguously, in window order, through a warp-aggregated atomic and
-// appends one segment record; records are radix-sorted by (pair, tile,
-// group) (pm_sort.cu) and the ordering pass (pm_order.cu) lays the hits out
-// as per-pair CSR lists sorted by location.
+// The candidates of a pair in a tile (or a 1024-window group of it) are
+// settled by the whole warp from a shared-memory queue; their hits are
+// written contiguously, in window order, behind one warp-aggregated atomic,
+// and one segment record describes them; records are radix-sorted by
+// (pair, tile, group) (pm_sort.cu) and the ordering pass (pm_order.cu) lays
+// the hits out as per-pair CSR lists sorted by location.
 //
 // pm_batch_create allocates everything once; pm_batch_run allocates nothing
 // and never waits on the host, so it can be captured in a CUDA graph and
@@ -44,12 +47,15 @@ constexpr uint32_t kKindShort = 0;   // pattern-sliced over positions 0..31, sha
 constexpr uint32_t kKindWs = 1;      // window-sliced (k <= kWsMaxK)
 constexpr uint32_t kKindLong = 2;    // pattern-sliced over all chunks (any k)
 constexpr uint32_t kKindShort2 = 3;  // pattern-sliced over positions 0..63, shared shifts (k <= 63)
-// Warp tiles per work item.  The last run of tiles of an item may reach past
-// the text by up to this many tiles minus one; the text's zero padding must
-// hold their copies (each tile copies 32*G + 2 blocks).
-constexpr int kMaxTilesPerItem = 4;
-static_assert((kMaxTilesPerItem + 1) * 32 * kGroups + 2 <= kPadBlocks,
-              "the text padding covers the last run of tiles");
+// categories of pairs (one launch each): window-sliced with k = 0..kWsMaxK, then these
+constexpr int kCatPs1 = kWsMaxK + 1;
+constexpr int kCatPs2 = kWsMaxK + 2;
+constexpr int kCatLong = kWsMaxK + 3;
+constexpr int kCats = kWsMaxK + 4;
+// Warp tiles per work item (the last run of tiles may reach past the text;
+// those tiles are neither copied nor evaluated).
+constexpr int kMaxTilesPerItem = 64;
+constexpr uint32_t kDefaultTilesPerItem = 16;
 }
 }  // namespace pm
 
@@ -58,8 +64,8 @@ struct pm_batch {
     uint32_t npat;
     uint32_t ngroups;
     uint32_t nphases;  // work-item rows: pieces of the categories of groups
-    int ws_max;        // largest k evaluated window-sliced (-1: none)
-    int grid;
+    uint32_t cat_rows[pm::kWsMaxK + 4][2];  // per category: its rows [first, end)
+    int grid;          // CTAs per launch (0: as many as each category's kernel keeps resident)
     int key_bits;
     uint32_t tiles;    // warp tiles per work item
     uint64_t ntiles;   // warp tiles of the longest window range
@@ -109,8 +115,19 @@ struct BatchArgs {
     uint32_t *status;
 };
 
+// Append one segment record: `count` hits of pair p at tmp[base ..], in
+// window order, for the (pair, tile, group) of `key`.  One lane calls it.
+__device__ __forceinline__ void put_record(const BatchArgs &ba, uint32_t p, unsigned long long key,
+                                           unsigned long long base, uint32_t count)
+{
+    atomicAdd(ba.pat_counts + p, (unsigned long long)count);
+    const unsigned long long r = atomicAdd(ba.rec_cursor, 1ull);
+    if (r < ba.rec_cap) ba.recs[r] = SegRecord{key, (uint32_t)base, count};
+}
+
 // Emit the hits of one 1024-window group (pass bits of every lane) in window
-// order through one warp-aggregated atomic, and append its segment record.
+// order through one warp-aggregated atomic, and append its segment record
+// (each lane counting its own hits: the path for dense hits).
 __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t p, uint64_t key,
                                            uint32_t nchunks, uint32_t k,
                                            const uint4 *__restrict__ M, const BatchArgs &ba)
@@ -129,9 +146,7 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
     unsigned long long base = 0;
     if (lane == 0) {
         base = atomicAdd(ba.cursor, (unsigned long long)total);
-        atomicAdd(ba.pat_counts + p, (unsigned long long)total);
-        const unsigned long long r = atomicAdd(ba.rec_cursor, 1ull);
-        if (r < ba.rec_cap) ba.recs[r] = SegRecord{key, (uint32_t)base, total};
+        put_record(ba, p, key, base, total);
     }
     base = __shfl_sync(kFull, base, 0);
     unsigned long long q = base + incl - nh;
@@ -147,35 +162,120 @@ __device__ __forceinline__ void emit_group(uint32_t pass, uint64_t blk, uint32_t
     }
 }
 
-// A pattern-sliced group over the first C chunks (C = 1: k <= 31, C = 2:
-// k <= 63): for each window the funnel shifts that line the text up with
-// the chunks are done once and serve all kP pairs of the group, whose masks
-// sit in shared memory.  Bytes of the multiply-add results hold
+// What a work item keeps in shared memory of each pair of its row.
+struct RowPair {
+    uint32_t p;        // pair index
+    uint32_t k;
+    uint32_t nchunks;
+    uint32_t masks;    // chunk 0 in the arena (uint4 units)
+    uint32_t lists;    // n_single | n_general << 8 (window-sliced list)
+    uint32_t ntiles;   // warp tiles holding windows of the pair
+    uint32_t nfull;    // warp tiles whose windows are all valid for the pair
+    uint32_t pad;
+    uint64_t nwin;
+};
+
+// Window-valid mask of the 32 windows of pair r that start in block blk of
+// warp tile `tile`.
+__device__ __forceinline__ uint32_t pair_valid(const RowPair &r, uint64_t tile, uint64_t blk)
+{
+    return tile < r.nfull ? kFull : valid_mask(blk, r.nwin);
+}
+
+// The candidates of pair rp in NG groups (g0 .. g0+NG-1) of one staged warp
+// tile, settled by the whole warp from its shared-memory queue q as in
+// settle_emit_queued (see pm_scan_impl.cuh), the hits written once and
+// described by one segment record whose key is that of group g0.  Returns
+// false, having done nothing, when there are more than kQueueCap candidates
+// or k >= 2^20.  Call with the whole warp.
+template <int NG>
+__device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], uint32_t g0, uint64_t tile,
+                                                   const uint2 *stage, uint32_t *q, const RowPair &rp,
+                                                   const BatchArgs &ba)
+{
+    static_assert(NG == 1 || NG == 4, "one group or a whole tile");
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t k = rp.k;
+    const uint4 *__restrict__ M = ba.arena + rp.masks;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) packed |= (uint32_t)__popc(cand[i]) << (8 * i);
+    const uint32_t total = __reduce_add_sync(kFull, (packed * 0x01010101u) >> 24);
+    if (total > kQueueCap || k >= (1u << 20)) return false;
+    uint32_t incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    const uint32_t pos = tot * 0x01010100u + (incl - packed);  // bytes never carry: total <= 255
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        uint32_t at = (pos >> (8 * i)) & 0xffu;
+        uint32_t m = cand[i];
+        while (m) {
+            const uint32_t w = __ffs(m) - 1;
+            m &= m - 1;
+            q[at++] = ((g0 + (uint32_t)i) << 10) | (lane << 5) | w;  // window within the tile
+        }
+    }
+    __syncwarp();
+    uint32_t hits = 0;
+    for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint32_t rec = 0;
+        bool hit = false;
+        if (i < total) {
+            const uint32_t e = q[i];
+            const uint32_t gl = e >> 5;  // block within the tile
+            const uint32_t c = candidate_count(stage + gl, tile * (32ull * G) + gl, e & 31u, M, 0u, rp.nchunks, k,
+                                               ba.planes, ba.unk);
+            hit = c <= k;
+            rec = e | (c << 12);
+        }
+        const uint32_t hb = __ballot_sync(kFull, hit);
+        __syncwarp();  // every entry of this round is read before any is overwritten
+        if (hit) q[hits + __popc(hb & ((1u << lane) - 1u))] = rec;
+        hits += __popc(hb);
+    }
+    if (hits) {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0) {
+            base = atomicAdd(ba.cursor, (unsigned long long)hits);
+            put_record(ba, rp.p, ((unsigned long long)rp.p * ba.ntiles + tile) * G + g0, base, hits);
+        }
+        base = __shfl_sync(kFull, base, 0);
+        const uint64_t w0 = tile * kTileWindows;
+        for (uint32_t i = lane; i < hits; i += 32) {
+            const uint32_t r = q[i];
+            if (base + i < ba.cap) ba.tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & 4095u)), r >> 12};
+        }
+    }
+    __syncwarp();  // the queue is rewritten next
+    return true;
+}
+
+// One pattern-sliced group over the first C chunks (C = 1: k <= 31, C = 2:
+// k <= 63) on one staged tile: for each window the funnel shifts that line
+// the text up with the chunks are done once and serve all kP pairs of the
+// group, whose masks sit in shared memory (sM0, sM1; sP {k in every byte};
+// loaded once per work item).  Bytes of the multiply-add results hold
 // (4/C) * (matches + k) <= (4/C) * (64C - 1) < 256, so bit 7 of a byte is set
 // exactly when matches + k >= 32C, i.e. when the window has at most k
-// mismatches in those positions.  Windows that pass and whose pattern is
-// longer are then counted exactly (settle_staged).
+// mismatches in those positions.  The candidates of each pair and group are
+// then settled by the warp together (settle_emit_record; each lane its own
+// when there are too many).
 // kAll: all kP slots hold pairs (every group but the last of a category);
 // otherwise the empty slots are skipped.
 template <int C, bool kAll>
-__device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t pfirst,
-                                            uint32_t cnt, uint4 *sM0, uint4 *sM1, uint4 *sP,
-                                            const BatchArgs &ba)
+__device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t cnt, const RowPair *rp,
+                                            const uint4 *sM0, const uint4 *sM1, const uint4 *sP, uint32_t *q,
+                                            uint32_t two, const BatchArgs &ba)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t two = ba.pats[ba.order[pfirst]].two;
     const uint32_t m1 = C == 1 ? two << 1 : two, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
-    if (lane < kP) {
-        // slots past cnt repeat a real pair (never evaluated)
-        const uint32_t pi = __ldg(ba.order + pfirst + lane);
-        const PatDesc &dl = ba.pats[pi];
-        const uint32_t kl = (uint32_t)dl.k;
-        sM0[lane] = __ldg(ba.arena + dl.masks);
-        if (C == 2)
-            sM1[lane] = dl.nchunks > 1 ? __ldg(ba.arena + dl.masks + 1) : make_uint4(kFull, kFull, kFull, kFull);
-        sP[lane] = make_uint4(pi, kl, kl * (m24 | m16 | m8 | m1), 0u);
-    }
-    __syncwarp();
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
         const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
@@ -184,19 +284,18 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
         uint32_t acc[kP];
 #pragma unroll
         for (int p = 0; p < kP; ++p) acc[p] = 0u;
-        // one step at a time: with the steps unrolled the kernel spills at
-        // every WSMAX and is larger (instruction fetch was its largest
-        // stall); one step at a time measured 1.7 % faster over 4096 pairs
+        // one step at a time: with the steps unrolled the kernel spills and
+        // is larger (instruction fetch was its largest stall)
 #pragma unroll 1
         for (uint32_t j = 0; j < 8; ++j) {
             uint32_t lo[4], hi[4], lo1[4], hi1[4];
 #pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
-                lo[q] = __funnelshift_r(ta.x, tb.x, 8 * q + j);
-                hi[q] = __funnelshift_r(ta.y, tb.y, 8 * q + j);
+            for (uint32_t qq = 0; qq < 4; ++qq) {
+                lo[qq] = __funnelshift_r(ta.x, tb.x, 8 * qq + j);
+                hi[qq] = __funnelshift_r(ta.y, tb.y, 8 * qq + j);
                 if (C == 2) {
-                    lo1[q] = __funnelshift_r(tb.x, c.x, 8 * q + j);
-                    hi1[q] = __funnelshift_r(tb.y, c.y, 8 * q + j);
+                    lo1[qq] = __funnelshift_r(tb.x, c.x, 8 * qq + j);
+                    hi1[qq] = __funnelshift_r(tb.y, c.y, 8 * qq + j);
                 }
             }
 #pragma unroll
@@ -205,13 +304,13 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 const uint4 M0 = sM0[p];
                 uint32_t gm[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) gm[q] = __popc(class_match(lo[q], hi[q], M0));
+                for (int qq = 0; qq < 4; ++qq) gm[qq] = __popc(class_match(lo[qq], hi[qq], M0));
                 if (C == 2) {
                     const uint4 M1 = sM1[p];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) gm[q] += __popc(class_match(lo1[q], hi1[q], M1));
+                    for (int qq = 0; qq < 4; ++qq) gm[qq] += __popc(class_match(lo1[qq], hi1[qq], M1));
                 }
-                uint32_t v = mad_lo(gm[3], m24, sP[p].z);
+                uint32_t v = mad_lo(gm[3], m24, sP[p].x);
                 v = mad_lo(gm[2], m16, v);
                 v = mad_lo(gm[1], m8, v);
                 v = mad_lo(gm[0], m1, v);
@@ -222,231 +321,257 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
             if (p < (int)cnt) {
-                const uint32_t pi = sP[p].x, kp = sP[p].y;
-                const PatDesc &d = ba.pats[pi];
-                const uint32_t valid = valid_mask(blk, d.nwin);
-                const uint4 *M = ba.arena + d.masks;
-                uint32_t pass = acc[p] & valid;
-                if (d.nchunks > (uint32_t)C)
-                    pass = settle_staged(pass, blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, d.nchunks,
-                                         kp, ba.planes);
-                if (__any_sync(kFull, pass != 0u))
-                    emit_group(pass, blk, pi, ((unsigned long long)pi * ba.ntiles + tile) * G + g,
-                               d.nchunks, kp, M, ba);
+                const RowPair &r = rp[p];
+                if (tile >= r.ntiles) continue;
+                uint32_t pass[1] = {acc[p] & pair_valid(r, tile, blk)};
+                if (!__any_sync(kFull, pass[0] != 0u)) continue;
+                if (!settle_emit_record<1>(pass, (uint32_t)g, tile, stage, q, r, ba)) {
+                    const uint4 *M = ba.arena + r.masks;
+                    if (r.nchunks > (uint32_t)C)
+                        pass[0] = settle_staged(pass[0], blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, r.nchunks,
+                                                r.k, ba.planes);
+                    if (__any_sync(kFull, pass[0] != 0u))
+                        emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
+                                   r.nchunks, r.k, M, ba);
+                }
             }
         }
     }
-    __syncwarp();  // the group's shared slots are rewritten by the next group
 }
 
-// WSMAX: the largest k of the batch's window-sliced pairs (0..6).
+// Window-sliced pair rp over one staged tile (a, b: the lane's blocks; list:
+// the pair's compact list in shared memory): the thermometer scan of
+// alive_window_sliced over the tile's four groups at once, the candidates
+// settled by the warp together.
+template <int K>
+__device__ __forceinline__ void ws_pair(const uint2 (&a)[G], const uint2 (&b)[G], const uint2 *stage,
+                                        uint64_t tile, const RowPair &rp, const uint32_t *list, uint32_t *q,
+                                        const BatchArgs &ba)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t valid[G], pass[G];
+    uint64_t blk[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+        valid[g] = pair_valid(rp, tile, blk[g]);
+    }
+    const bool cut =
+        alive_window_sliced<K>(a, b, list, rp.lists & 0xffu, rp.lists >> 8, ws_cut(K), valid, pass);
+    uint32_t anyp = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) anyp |= pass[g];
+    if (__any_sync(kFull, anyp != 0u) && !settle_emit_record<G>(pass, 0u, tile, stage, q, rp, ba)) {
+        const uint4 *M = ba.arena + rp.masks;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t ps = (cut || rp.nchunks > 1)
+                                    ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, rp.nchunks, rp.k, ba.planes)
+                                    : pass[g];
+            if (__any_sync(kFull, ps != 0u))
+                emit_group(ps, blk[g], rp.p, ((unsigned long long)rp.p * ba.ntiles + tile) * G + g, rp.nchunks,
+                           rp.k, M, ba);
+        }
+    }
+}
+
+// CAT: the category of every row of the launch (one launch per category
+// present, so that each kernel carries only its own evaluation: one kernel
+// holding every kind stalled on instruction fetch): 0..kWsMaxK window-sliced
+// pairs with k = CAT, then kCatPs1, kCatPs2, kCatLong.
 //
-// Each warp walks its own sequence of staged tiles: position s of the
-// sequence is tile s % T of work item first + (s / T) * stride, where an item
-// is a run of T warp tiles crossed with a row of groups (items row-major:
-// all warps work on one kind of group at a time).  The sequence is staged
-// two positions ahead into a two-stage ring; a stage is refilled once the
-// warp is done with its tile.
-template <int WSMAX>
+// A row is one group of up to kP pairs; a work item is a run of T warp
+// tiles crossed with a row, items numbered run-major (item = run * rows +
+// row), so the warps at work at any time cover a few runs of tiles with
+// every row: each text tile is read from device memory once and then from
+// L2.  A warp loads its item's row (the pairs' descriptors and masks or
+// position lists) into shared memory once, then walks the item's tiles;
+// the tiles of its whole sequence of items are staged kStages ahead by the
+// lanes' own asynchronous copies, and a stage is refilled once the warp is
+// done with its tile.
+template <int CAT>
 __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArgs ba)
 {
-    __shared__ __align__(128) uint2 sbuf[kScanWarps][2][kStageBlocks];
-    __shared__ __align__(8) uint64_t sbar[kScanWarps][2];
+    constexpr bool kWsCat = CAT <= kWsMaxK;
+    constexpr uint32_t S = kStages;
+    constexpr uint32_t kSB = scan_stage_blocks<G>();
+    __shared__ __align__(128) uint2 sbuf[kScanWarps][S][kSB];
+    __shared__ uint32_t squeue[kScanWarps][kQueueCap];
+    __shared__ RowPair srow[kScanWarps][kP];
+    __shared__ uint32_t slist[kScanWarps][kWsCat ? kP : 1][32];
     __shared__ uint4 sM0[kScanWarps][kP];
     __shared__ uint4 sM1[kScanWarps][kP];
-    __shared__ uint4 sP[kScanWarps][kP];  // pattern-sliced group: {pair, k, k in every byte, 0}
+    __shared__ uint4 sP[kScanWarps][kP];  // pattern-sliced group: {k in every byte, 0, 0, 0}
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        dev::mbar_init(&sbar[warp][0], 1);
-        dev::mbar_init(&sbar[warp][1], 1);
-        dev::fence_mbar_init();
-    }
-    __syncwarp();
-
-    // runs < 2^21 (a text has fewer than 2^32 symbols) and the grid is
-    // resident, so 32-bit positions suffice
     const uint32_t stride = gridDim.x * kScanWarps;
     const uint32_t T = ba.tiles;
-    const uint32_t runs = (uint32_t)ba.runs;
     const uint32_t nrows = (uint32_t)(ba.items / ba.runs);
-    // Sequence positions as (row, run, tile within the run of T): work item
-    // row * runs + run.  Moving on by `stride` items needs no division (this
-    // runs once per tile; a 64-bit division would cost more than a cheap
-    // tile's evaluation).
-    struct Pos {
-        uint32_t row, u, run;
-    };
-    auto advance = [&](Pos &q) {
-        if (++q.u == T) {
-            q.u = 0;
-            q.run += stride;
-            while (q.run >= runs && q.row < nrows) {
-                q.run -= runs;
-                ++q.row;
-            }
-        }
-    };
-    auto tile_of = [&](const Pos &q) { return (uint64_t)q.run * T + q.u; };
+    const uint32_t items = (uint32_t)ba.items;  // runs * rows < 2^31 (the planner widens the runs)
+    const uint64_t ntiles = ba.ntiles;
+    // the tile of position u of item i (tiles past the text are never copied nor evaluated)
+    auto tile_of = [&](uint32_t i, uint32_t u) { return (uint64_t)(i / nrows) * T + u; };
+
     const uint32_t first = blockIdx.x * kScanWarps + warp;
-    Pos cp{first / runs, 0u, first % runs};  // consumed
-    if (cp.row > nrows) cp.row = nrows;
-    Pos pp = cp;                                                  // next to stage
+    uint32_t pi = first, pu = 0;  // next position to stage
 #pragma unroll
-    for (int st = 0; st < 2; ++st) {
-        if (lane == 0 && pp.row < nrows) issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
-        advance(pp);
+    for (uint32_t st = 0; st < S; ++st) {
+        if (pi < items) {
+            const uint64_t t = tile_of(pi, pu);
+            if (t < ntiles) copy_tile_async<G>(ba.planes, t * (32u * G), &sbuf[warp][st][0], lane);
+        }
+        cp_async_commit();
+        if (++pu == T) {
+            pu = 0;
+            pi += stride;
+        }
     }
 
-    for (uint64_t s = 0; cp.row < nrows; ++s, advance(cp)) {
-        const int st = (int)(s & 1);
-        const uint32_t par = (uint32_t)(s >> 1) & 1u;
-        const uint64_t tile = tile_of(cp);
-        const bool ok = dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
-        if (__any_sync(kFull, !ok)) {
-            if (lane == 0) {
-                atomicOr(ba.status, kDevTimeout);
-                // let the copies this warp still has in flight land before it leaves
-                dev::mbar_wait_bounded(&sbar[warp][st], par, kWaitLimitNs);
-                Pos nq = cp;
-                advance(nq);
-                if (nq.row < nrows)
-                    dev::mbar_wait_bounded(&sbar[warp][st ^ 1], (uint32_t)((s + 1) >> 1) & 1u, kWaitLimitNs);
+    uint32_t st = 0;
+    for (uint32_t item = first; item < items; item += stride) {
+        // ---- the item's row into shared memory ----
+        const uint32_t row = item % nrows;
+        const uint2 ph = __ldg(ba.phases + row);  // one group
+        const uint32_t grp = ph.x;
+        const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
+        __syncwarp();  // the previous item is done with the row's slots
+        if (lane < (int)cnt) {
+            const uint32_t p = __ldg(ba.order + grp * kP + lane);
+            const PatDesc &d = ba.pats[p];
+            RowPair r;
+            r.p = p;
+            r.k = (uint32_t)d.k;
+            r.nchunks = d.nchunks;
+            r.masks = (uint32_t)d.masks;
+            r.lists = d.n_single | (d.n_general << 8);
+            r.ntiles = (uint32_t)d.ntiles;
+            r.nfull = (uint32_t)(d.nwin / kTileWindows);
+            r.pad = 0;
+            r.nwin = d.nwin;
+            srow[warp][lane] = r;
+            if constexpr (!kWsCat) {
+                const uint32_t two = d.two;
+                const uint32_t m1 = CAT == kCatPs1 ? two << 1 : two;
+                sM0[warp][lane] = __ldg(ba.arena + d.masks);
+                sM1[warp][lane] = d.nchunks > 1 ? __ldg(ba.arena + d.masks + 1) : make_uint4(kFull, kFull, kFull, kFull);
+                sP[warp][lane] = make_uint4(r.k * ((m1 << 24) | (m1 << 16) | (m1 << 8) | m1), 0u, 0u, 0u);
             }
-            return;
         }
-        const uint2 *stage = &sbuf[warp][st][0];
-        const uint2 ph = __ldg(ba.phases + cp.row);
-        const uint32_t kind0 = __ldg(ba.gkind + ph.x) & 3u;  // a row holds one kind
-        if (kind0 == kKindWs) {
-            // The window-sliced evaluation needs only the lane's two blocks per
-            // group: take them into registers and refill the stage now, two
-            // tiles ahead (its items are short; a refill after the item would
-            // leave the next copy too little time to land).
-            uint2 a[G], b[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                a[g] = stage[32 * g + lane];
-                b[g] = stage[32 * g + lane + 1];
-            }
+        if constexpr (kWsCat) {
             __syncwarp();
-            if (lane == 0 && pp.row < nrows) {
-                dev::fence_proxy_async_smem();
-                issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
-            }
-            advance(pp);
-            for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
-                const uint32_t pfirst = grp * kP;
-                const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
-                {
-                    // ---- window-sliced group: one pattern at a time over all groups ----
-                    for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t p = __ldg(ba.order + pfirst + i);
-                        const PatDesc d = ba.pats[p];
-                        uint64_t blk[G];
-                        uint32_t valid[G], pass[G];
-                        uint32_t anyv = 0;
-#pragma unroll
-                        for (int g = 0; g < G; ++g) {
-                            blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                            valid[g] = valid_mask(blk[g], d.nwin);
-                            anyv |= valid[g];
-                        }
-                        if (!__any_sync(kFull, anyv != 0u)) continue;
-                        const uint4 *list = ba.arena + d.wslist;
-                        bool cut;
-                        // only the thresholds this batch uses are compiled in (instruction cache)
-                        if (d.k == 0) cut = alive_window_sliced<0, true>(a, b, list, d.n_single, d.n_general, ws_cut(0), valid, pass);
-                        else if (WSMAX >= 1 && d.k == 1) cut = alive_window_sliced<(WSMAX >= 1 ? 1 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 1 ? 1 : 0)), valid, pass);
-                        else if (WSMAX >= 2 && d.k == 2) cut = alive_window_sliced<(WSMAX >= 2 ? 2 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 2 ? 2 : 0)), valid, pass);
-                        else if (WSMAX >= 3 && d.k == 3) cut = alive_window_sliced<(WSMAX >= 3 ? 3 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 3 ? 3 : 0)), valid, pass);
-                        else if (WSMAX >= 4 && d.k == 4) cut = alive_window_sliced<(WSMAX >= 4 ? 4 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 4 ? 4 : 0)), valid, pass);
-                        else if (WSMAX >= 5 && d.k == 5) cut = alive_window_sliced<(WSMAX >= 5 ? 5 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 5 ? 5 : 0)), valid, pass);
-                        else cut = alive_window_sliced<(WSMAX >= 6 ? 6 : 0), true>(a, b, list, d.n_single, d.n_general, ws_cut((WSMAX >= 6 ? 6 : 0)), valid, pass);
-                        const uint4 *M = ba.arena + d.masks;
-#pragma unroll
-                        for (int g = 0; g < G; ++g) {
-                            const uint32_t ps = (cut || d.nchunks > 1)
-                                ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, d.nchunks, (uint32_t)d.k,
-                                                   ba.planes)
-                                : pass[g];
-                            if (__any_sync(kFull, ps != 0u))
-                                emit_group(ps, blk[g], p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                           d.nchunks, (uint32_t)d.k, M, ba);
-                        }
-                    }
+            // kP compact lists of at most 32 words
+            for (uint32_t i = lane; i < cnt * 32u; i += 32) {
+                const RowPair &r = srow[warp][i >> 5];
+                const uint32_t len = (r.lists & 0xffu) + (r.lists >> 8);
+                const uint32_t w = i & 31u;
+                if (w < len) {
+                    const uint32_t p = r.p;
+                    slist[warp][i >> 5][w] = __ldg((const uint32_t *)(ba.arena + ba.pats[p].wslist) + w);
                 }
             }
-        } else {
-            // pattern-sliced groups read the staged tile while they settle the
-            // windows that survive their first chunks (and the every-chunk
-            // groups read it per group): refill after the item
-            for (uint32_t grp = ph.x; grp < ph.y; ++grp) {
-                const uint32_t pfirst = grp * kP;
-                const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
-                if (kind0 == kKindLong) {
-                    // ---- every chunk counted, one pattern at a time ----
+        }
+        __syncwarp();
+        const uint32_t two = ba.pats[srow[warp][0].p].two;
+
+        for (uint32_t u = 0; u < T; ++u) {
+            cp_async_wait<S - 1>();  // this tile's group has landed
+            __syncwarp();
+            const uint64_t tile = tile_of(item, u);
+            const uint2 *stage = &sbuf[warp][st][0];
+            if (tile < ntiles) {
+                if constexpr (kWsCat) {
+                    uint2 a[G], b[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        a[g] = stage[32 * g + lane];
+                        b[g] = stage[32 * g + lane + 1];
+                    }
                     for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t p = __ldg(ba.order + pfirst + i);
-                        const PatDesc d = ba.pats[p];
-                        const uint4 *M = ba.arena + d.masks;
+                        const RowPair &r = srow[warp][i];
+                        if (tile >= r.ntiles) continue;  // this pair's windows end before the tile
+                        ws_pair<CAT>(a, b, stage, tile, r, slist[warp][i], squeue[warp], ba);
+                    }
+                } else if constexpr (CAT == kCatLong) {
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const RowPair &r = srow[warp][i];
+                        if (tile >= r.ntiles) continue;
+                        const uint4 *M = ba.arena + r.masks;
 #pragma unroll 1
                         for (int g = 0; g < G; ++g) {
                             const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-                            const uint32_t valid = valid_mask(blk, d.nwin);
-                            const uint32_t pass = pass_multi_chunk(ba.planes, blk, M, d.nchunks, (uint32_t)d.k,
-                                                                   valid, stage[32 * g + lane],
-                                                                   stage[32 * g + lane + 1]);
-                            if (__any_sync(kFull, pass != 0u))
-                                emit_group(pass, blk, p, ((unsigned long long)p * ba.ntiles + tile) * G + g,
-                                           d.nchunks, (uint32_t)d.k, M, ba);
+                            uint32_t pass[1] = {pass_multi_chunk(ba.planes, blk, M, r.nchunks, r.k,
+                                                                 pair_valid(r, tile, blk), stage[32 * g + lane],
+                                                                 stage[32 * g + lane + 1])};
+                            if (__any_sync(kFull, pass[0] != 0u) &&
+                                !settle_emit_record<1>(pass, (uint32_t)g, tile, stage, squeue[warp], r, ba))
+                                emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
+                                           r.nchunks, r.k, M, ba);
                         }
                     }
-                } else if (kind0 == kKindShort) {
-                    if (cnt == kP) short_group<1, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-                    else short_group<1, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
                 } else {
-                    if (cnt == kP) short_group<2, true>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
-                    else short_group<2, false>(stage, tile, pfirst, cnt, sM0[warp], sM1[warp], sP[warp], ba);
+                    constexpr int C = CAT == kCatPs1 ? 1 : 2;
+                    if (cnt == kP)
+                        short_group<C, true>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp],
+                                             squeue[warp], two, ba);
+                    else
+                        short_group<C, false>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp],
+                                              squeue[warp], two, ba);
                 }
             }
+            // refill this stage with the position S ahead
             __syncwarp();
-            if (lane == 0 && pp.row < nrows) {
-                dev::fence_proxy_async_smem();
-                issue_tile(ba.planes, tile_of(pp), &sbuf[warp][st][0], &sbar[warp][st]);
+            if (pi < items) {
+                const uint64_t t = tile_of(pi, pu);
+                if (t < ntiles) copy_tile_async<G>(ba.planes, t * (32u * G), &sbuf[warp][st][0], lane);
             }
-            advance(pp);
+            cp_async_commit();
+            if (++pu == T) {
+                pu = 0;
+                pi += stride;
+            }
+            if (++st == S) st = 0;
         }
     }
+    cp_async_wait<0>();  // nothing in flight when the warp leaves
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-const void *batched_kernel(int ws_max)
+template <int CAT>
+const void *batched_ptr()
 {
-    switch (ws_max < 0 ? 0 : ws_max) {
-    case 0: return (const void *)&k_scan_batched<0>;
-    case 1: return (const void *)&k_scan_batched<1>;
-    case 2: return (const void *)&k_scan_batched<2>;
-    case 3: return (const void *)&k_scan_batched<3>;
-    case 4: return (const void *)&k_scan_batched<4>;
-    case 5: return (const void *)&k_scan_batched<5>;
-    default: return (const void *)&k_scan_batched<6>;
-    }
+    return (const void *)&k_scan_batched<CAT>;
 }
 
-int batched_grid(int device, int ws_max)
+const void *batched_kernel(int cat)
 {
-    static std::atomic<int> cache[64][8];  // 0 = not yet computed
-    if (device < 0 || device >= 64) return 0;
-    const int slot = ws_max < 0 ? 0 : (ws_max > 6 ? 6 : ws_max);
-    if (const int g = cache[device][slot].load(std::memory_order_relaxed)) return g;
+    switch (cat) {
+    case 0: return batched_ptr<0>();
+    case 1: return batched_ptr<1>();
+    case 2: return batched_ptr<2>();
+    case 3: return batched_ptr<3>();
+    case 4: return batched_ptr<4>();
+    case 5: return batched_ptr<5>();
+    case 6: return batched_ptr<6>();
+    case kCatPs1: return batched_ptr<kCatPs1>();
+    case kCatPs2: return batched_ptr<kCatPs2>();
+    default: return batched_ptr<kCatLong>();
+    }
+}
+static_assert(kWsMaxK == 6, "one window-sliced launch per k = 0 .. 6");
+
+// CTAs a launch of category cat keeps resident on the device.
+int batched_grid(int device, int cat)
+{
+    static std::atomic<int> cache[64][kCats];  // 0 = not yet computed
+    if (device < 0 || device >= 64 || cat < 0 || cat >= kCats) return 0;
+    if (const int g = cache[device][cat].load(std::memory_order_relaxed)) return g;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(slot), kScanThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(cat), kScanThreads, 0);
     const int g = sms * (per_sm < 1 ? 1 : per_sm);
-    cache[device][slot].store(g, std::memory_order_relaxed);
+    cache[device][cat].store(g, std::memory_order_relaxed);
     return g;
 }
 
@@ -462,7 +587,7 @@ struct BatchPlan {
     std::vector<uint4> arena;
     std::vector<uint32_t> order, gkind;
     std::vector<uint2> phases;
-    int ws_max = -1;
+    uint32_t cat_rows[kWsMaxK + 4][2] = {};
     int grid = 0;
     uint32_t tiles = 1;
     uint64_t ntiles = 0, runs = 0;
@@ -513,10 +638,9 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
     const int ws_max = below(o.ws_below, 5) - 1;  // -1: none
     const int ps1_max = below(o.ps1_below, 18) - 1;
     const int ps2_max = below(o.ps2_below, 41) - 1;
-    const uint32_t tiles = o.tiles > 0 ? (uint32_t)o.tiles : 1u;
-    // rows of 2 groups by default: measured faster than whole categories for
-    // the pattern-sliced kinds (k = 16..31: 4-20 %), equal for the others
-    const uint32_t groups_per_row = o.group > 0 ? (uint32_t)((o.group + kP - 1) / kP) : 2u;
+    uint32_t tiles = o.tiles > 0 ? (uint32_t)o.tiles : kDefaultTilesPerItem;
+    // a row is one group of kP pairs (o.group is accepted and not used)
+    const uint32_t groups_per_row = 1u;
 
     // descriptors and arena
     std::vector<PatDesc> &desc = pl.desc;
@@ -531,9 +655,9 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
             const uint64_t mo = arena.size();
             arena.insert(arena.end(), pt->masks, pt->masks + pt->nchunks);
             const uint64_t lo = arena.size();
-            uint4 list[64];  // at most 2 entries per position of the first 32
-            ordered_wslist(pt, text, list);
-            arena.insert(arena.end(), list, list + pt->n_single + 2 * pt->n_general);
+            uint4 list[8] = {};  // one word per position of the first 32
+            ordered_wslist(pt, text, (uint32_t *)list);
+            arena.insert(arena.end(), list, list + wslist_units(pt));
             it = where.emplace(pt, std::make_pair(mo, lo)).first;
         }
         PatDesc &d = desc[p];
@@ -559,10 +683,9 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
 
     // Categories: window-sliced pairs with k = 0, 1, ..., then pattern-sliced
     // pairs over one chunk, over two chunks, and over all chunks.  Within a
-    // category pairs are ordered by m and cut into groups of kP; the groups
-    // of a category are cut into rows of groups_per_row.  A work item is a
-    // row crossed with a run of `tiles` warp tiles, rows outermost, so all
-    // warps run one kind of evaluation at a time.
+    // category pairs are ordered by m and cut into groups of kP, one row
+    // each.  A work item is a row crossed with a run of `tiles` warp tiles;
+    // each category runs as its own launch, items numbered run-major.
     std::vector<std::vector<uint32_t>> cats(kWsMaxK + 4);
     for (uint32_t p = 0; p < npat; ++p) {
         const int32_t kp = desc[p].k;
@@ -591,13 +714,17 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
             pl.gkind.push_back(kind | (count << 2));
         }
         const uint32_t g1 = (uint32_t)pl.gkind.size();
+        pl.cat_rows[c][0] = (uint32_t)pl.phases.size();
         for (uint32_t r = g0; r < g1; r += std::min(groups_per_row, g1 - r))
             pl.phases.push_back(make_uint2(r, r + std::min(groups_per_row, g1 - r)));
+        pl.cat_rows[c][1] = (uint32_t)pl.phases.size();
     }
-    pl.ws_max = ws_max;
-    pl.grid = o.grid > 0 ? o.grid : batched_grid(dev, ws_max);
-    pl.tiles = tiles;
+    pl.grid = o.grid > 0 ? o.grid : 0;
     pl.ntiles = min_m <= text->n ? (text->n - min_m + 1 + kTileWindows - 1) / kTileWindows : 0;
+    // item numbers (runs * rows of a category) stay below 2^31
+    const uint64_t rows = std::max<uint64_t>(pl.phases.size(), 1);
+    while ((pl.ntiles + tiles - 1) / tiles * rows >= (1ull << 31)) tiles *= 2;
+    pl.tiles = tiles;
     pl.runs = (pl.ntiles + tiles - 1) / tiles;
     const unsigned long long max_key = (unsigned long long)npat * (pl.ntiles ? pl.ntiles : 1) * G;
     pl.key_bits = 0;
@@ -650,7 +777,7 @@ void fill_batch(const BatchPlan &pl, const pm_text *text, uint32_t npat, uint64_
     b->device = dev;
     b->npat = npat;
     b->ngroups = (uint32_t)pl.gkind.size();
-    b->ws_max = pl.ws_max;
+    std::memcpy(b->cat_rows, pl.cat_rows, sizeof b->cat_rows);
     b->grid = pl.grid;
     b->ntiles = pl.ntiles;
     b->tiles = pl.tiles;
@@ -693,17 +820,21 @@ pm_status run_batch(const pm_batch *b, pm_hit *hits, uint64_t *offsets, cudaStre
         rc = cuda_status(cudaMemsetAsync(b->pat_counts, 0, b->npat * sizeof(unsigned long long), st),
                          "clear counts");
     if (rc) return rc;
-    const uint64_t items = b->runs * b->nphases;
-    if (items > 0) {
-        BatchArgs ba{b->planes, b->unk, b->pats,  b->order,  b->gkind, b->phases,  b->arena,
+    // one persistent launch per category present, back to back on the stream
+    for (int cat = 0; !rc && cat < kCats; ++cat) {
+        const uint32_t r0 = b->cat_rows[cat][0], r1 = b->cat_rows[cat][1];
+        const uint64_t items = b->runs * (uint64_t)(r1 - r0);
+        if (items == 0) continue;
+        BatchArgs ba{b->planes, b->unk, b->pats,  b->order,  b->gkind, b->phases + r0, b->arena,
                      b->npat,   b->ngroups, b->tiles, b->ntiles, b->runs, items,
                      b->tmp,    b->capacity, cursor,  b->recs,  b->capacity, rec_cursor,
                      b->pat_counts, status};
         uint64_t grid = (items + kScanWarps - 1) / kScanWarps;
-        if (grid > (uint64_t)b->grid) grid = (uint64_t)b->grid;
+        const int lim = b->grid > 0 ? b->grid : batched_grid(b->device, cat);
+        if (grid > (uint64_t)lim) grid = (uint64_t)lim;
         void *args[] = {(void *)&ba};
-        rc = cuda_status(cudaLaunchKernel(batched_kernel(b->ws_max), dim3((unsigned)grid),
-                                          dim3(kScanThreads), args, 0, st),
+        rc = cuda_status(cudaLaunchKernel(batched_kernel(cat), dim3((unsigned)grid), dim3(kScanThreads), args, 0,
+                                          st),
                          "batched scan kernel");
     }
     SegRecord *sorted = b->recs;

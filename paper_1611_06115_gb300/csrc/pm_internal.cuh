@@ -65,11 +65,15 @@ struct TraceRange {
 // windows die as early as possible (the early stop of Sec. 2.4 then ends the
 // scan sooner; the sum of Eq. 4 does not depend on the order): one-letter
 // entries by increasing frequency of their letter in t (ties by letter, so
-// that each letter's entries form one run; every entry's z field receives
-// the index one past the end of its run), then the class entries by
-// increasing frequency of their letters.  Stable; out receives n_single +
-// 2 * n_general entries.
-inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
+// that each letter's entries form one run), then the class entries by
+// increasing frequency of their letters.  Stable.  `out` receives the list
+// in the kernels' compact form, one 32-bit word per listed position
+// (n_single + n_general words, at most 32):
+//   one-letter entry  bits 0-4 the position j, bits 5-6 the letter's Table 1
+//                     code, bits 8-13 the index one past the end of its run;
+//   class entry       bits 0-4 the position j, bits 16-19 the class's
+//                     membership (A, C, G, T), bit 31 set.
+inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint32_t *out)
 {
     const uint32_t ns = p->n_single, ng = p->n_general;
     uint32_t idx[64];
@@ -95,14 +99,27 @@ inline void ordered_wslist(const pm_pattern *p, const pm_text *t, uint4 *out)
     };
     sort_range(0, ns);
     sort_range(ns, ns + ng);
-    for (uint32_t i = 0; i < ns; ++i) out[i] = p->wslist[idx[i]];
-    for (uint32_t i = ns; i-- > 0;)
-        out[i].z = (i + 1 < ns && out[i + 1].y == out[i].y) ? out[i + 1].z : i + 1;
+    uint32_t code[32];
+    for (uint32_t i = 0; i < ns; ++i) {
+        const uint4 e = p->wslist[idx[i]];
+        code[i] = e.y & 3u;
+        out[i] = (e.x & 31u) | (code[i] << 5);
+    }
+    uint32_t end = ns;
+    for (uint32_t i = ns; i-- > 0;) {
+        if (i + 1 < ns && code[i + 1] != code[i]) end = i + 1;
+        out[i] |= end << 8;
+    }
     for (uint32_t i = 0; i < ng; ++i) {
-        out[ns + 2 * i] = p->wslist[ns + 2 * idx[ns + i]];
-        out[ns + 2 * i + 1] = p->wslist[ns + 2 * idx[ns + i] + 1];
+        const uint32_t j = p->wslist[ns + 2 * idx[ns + i]].x;
+        const uint4 mem = p->wslist[ns + 2 * idx[ns + i] + 1];
+        out[ns + i] = (j & 31u) | ((mem.x & 1u) << 16) | ((mem.y & 1u) << 17) | ((mem.z & 1u) << 18) |
+                      ((mem.w & 1u) << 19) | (1u << 31);
     }
 }
+
+// uint4 units the compact list of p takes in an arena (four words each).
+inline uint32_t wslist_units(const pm_pattern *p) { return (p->n_single + p->n_general + 3) / 4; }
 
 constexpr int kScanThreads = 256;                        // threads per scan CTA
 constexpr int kScanWarps = kScanThreads / 32;
@@ -132,7 +149,8 @@ struct PatDesc {
     uint32_t c0;         // pattern-sliced scan kernels: the chunk their first stage tests
                          //   (first_stage_chunk); 0 everywhere else
     uint64_t masks;      // chunk 0 in the arena (uint4 units)
-    uint64_t wslist;     // window-sliced list in the arena (uint4 units)
+    uint64_t wslist;     // window-sliced list (compact words, see ordered_wslist) in the arena
+                         //   (offset in uint4 units)
     uint64_t nwin;       // windows: n - m + 1, or 0 when m > n
     uint64_t tile0;      // first tile-table entry of this pattern
     uint64_t ntiles;     // warp tiles: ceil(nwin / windows per tile of the kernel that runs)

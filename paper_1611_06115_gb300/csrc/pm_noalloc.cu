@@ -127,7 +127,7 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
             mo = nmask;
             distinct[ndistinct] = pt;
             where[ndistinct++] = mo;
-            nmask += pt->nchunks + pt->n_single + 2ull * pt->n_general;
+            nmask += pt->nchunks + wslist_units(pt);
         }
         PatDesc &d = desc[p];
         d.m = pt->m;
@@ -179,9 +179,9 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
         rc = cuda_status(cudaMemcpyAsync(d_masks + where[q], pt->masks, pt->nchunks * sizeof(uint4),
                                          cudaMemcpyHostToDevice, st),
                          "upload masks");
-        const uint64_t nl = pt->n_single + 2ull * pt->n_general;
-        uint4 list[64];  // at most 2 entries per position of the first 32
-        ordered_wslist(pt, text, list);
+        const uint64_t nl = wslist_units(pt);
+        uint4 list[8] = {};  // one word per position of the first 32
+        ordered_wslist(pt, text, (uint32_t *)list);
         if (!rc && nl)
             rc = cuda_status(cudaMemcpyAsync(d_masks + where[q] + pt->nchunks, list,
                                              nl * sizeof(uint4), cudaMemcpyHostToDevice, st),

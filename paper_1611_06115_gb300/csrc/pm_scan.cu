@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
     constexpr uint32_t S = kStages;
 
     __shared__ __align__(128) uint2 sbuf[kScanWarps][S][scan_stage_blocks<G>()];
-    __shared__ uint4 slist[kWS ? 64 : 1];
+    __shared__ uint32_t slist[kWS ? 32 : 1];
     __shared__ uint32_t squeue[kScanWarps][kQueueCap];
 
     const int warp = threadIdx.x >> 5;
@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 
     const PsConst pc = ps_const(d.two, (uint32_t)d.k);
 
     if (kWS) {
-        const uint32_t len = d.n_single + 2 * d.n_general;
-        for (uint32_t i = threadIdx.x; i < len; i += kScanThreads) slist[i] = __ldg(arena + d.wslist + i);
+        const uint32_t len = d.n_single + d.n_general;  // at most 32 words
+        const uint32_t *wl = (const uint32_t *)(arena + d.wslist);
+        for (uint32_t i = threadIdx.x; i < len; i += kScanThreads) slist[i] = __ldg(wl + i);
         __syncthreads();  // the only CTA-wide barrier: the list is shared by all warps
     }
     const uint32_t ntiles = (uint32_t)d.ntiles;

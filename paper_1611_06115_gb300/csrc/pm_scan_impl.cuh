@@ -125,10 +125,11 @@ __device__ __forceinline__ uint32_t pass_pattern_sliced(uint2 a, uint2 b, uint2 
     return pass;
 }
 
-// A position-list entry from shared memory, or from global memory through
-// the read-only path (every lane reads the same address: one broadcast).
+// A position-list entry (the compact words of ordered_wslist) from shared
+// memory, or from global memory through the read-only path (every lane reads
+// the same address: one broadcast).
 template <bool kGlobal>
-__device__ __forceinline__ uint4 ld_list(const uint4 *p)
+__device__ __forceinline__ uint32_t ld_list(const uint32_t *p)
 {
     if constexpr (kGlobal) return __ldg(p);
     else return *p;
@@ -189,7 +190,7 @@ constexpr int kWsCut = 2;   // `cut` entries tested, some window alive
 // run boundaries, as if the list were one run.
 template <int K, int CODE, bool kGlobal, int G>
 __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&b)[G],
-                                             const uint4 *__restrict__ list, uint32_t &e,
+                                             const uint32_t *__restrict__ list, uint32_t &e,
                                              uint32_t end, uint32_t cut, uint32_t (&L)[G][K + 1])
 {
     uint32_t pa[G], pb[G];
@@ -207,7 +208,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
     };
     // single entries up to the next multiple of S
     while (e < end && (e & (S - 1)) != 0) {
-        const uint32_t s0 = ld_list<kGlobal>(list + e).x;
+        const uint32_t s0 = ld_list<kGlobal>(list + e);  // bits 0-4 the shift (taken modulo 32)
 #pragma unroll
         for (int g = 0; g < G; ++g) add_position<K>(L[g], __funnelshift_r(pa[g], pb[g], s0));
         ++e;
@@ -220,7 +221,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
     while (e + S <= end) {
         uint32_t s[S];
 #pragma unroll
-        for (uint32_t u = 0; u < S; ++u) s[u] = ld_list<kGlobal>(list + e + u).x;
+        for (uint32_t u = 0; u < S; ++u) s[u] = ld_list<kGlobal>(list + e + u);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             if constexpr (K == 0) {
@@ -236,7 +237,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
     }
     // the rest of the run (fewer than S entries: no multiple of S is reached)
     for (; e < end; ++e) {
-        const uint32_t s0 = ld_list<kGlobal>(list + e).x;
+        const uint32_t s0 = ld_list<kGlobal>(list + e);
 #pragma unroll
         for (int g = 0; g < G; ++g) add_position<K>(L[g], __funnelshift_r(pa[g], pb[g], s0));
     }
@@ -245,10 +246,10 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
 
 // Window-sliced first chunk with a thermometer counter of K+1 levels over the
 // listed positions, for all groups of the lane at once.  The list (built by
-// pm_compile_pattern, ordered for the text by the host) holds first the
-// one-letter positions {shift, letter code, end of the run of that letter,
-// 0}, grouped into runs by letter, then pairs {shift, 0, 0, 0}, {A, C, G, T}
-// (membership broadcast) for the other classes.  alive[g] receives the
+// pm_compile_pattern, ordered for the text and packed by ordered_wslist)
+// holds first the one-letter positions (shift, letter code, end of the run
+// of that letter), grouped into runs by letter, then the other classes
+// (shift, membership).  alive[g] receives the
 // windows still at or below K.  After `cut` list entries the scan stops if
 // some window is still alive and returns true: the few candidates left are
 // cheaper to count one by one than to carry the whole tile through the
@@ -256,7 +257,7 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
 // (alive is then exact over the first 32 positions) or every window died.
 template <int K, bool kGlobal = false, int G>
 __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
-                                                    const uint4 *__restrict__ list,
+                                                    const uint32_t *__restrict__ list,
                                                     uint32_t n_single, uint32_t n_general,
                                                     uint32_t cut, const uint32_t (&valid)[G],
                                                     uint32_t (&alive)[G])
@@ -268,12 +269,13 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
         for (int i = 0; i <= K; ++i) L[g][i] = ~valid[g];  // invalid windows sit at every level
     uint32_t e = 0;
     while (e < n_single) {
-        const uint4 h = ld_list<kGlobal>(list + e);
+        const uint32_t h = ld_list<kGlobal>(list + e);
         // a run ends past its first entry and inside the list (also for a
         // malformed list, so that the loop always advances)
-        const uint32_t end = h.z > e ? (h.z < n_single ? h.z : n_single) : e + 1;
+        const uint32_t he = (h >> 8) & 63u;
+        const uint32_t end = he > e ? (he < n_single ? he : n_single) : e + 1;
         int r;
-        switch (h.y & 3u) {
+        switch ((h >> 5) & 3u) {
         case 0: r = ws_letter_run<K, 0, kGlobal, G>(a, b, list, e, end, cut, L); break;
         case 1: r = ws_letter_run<K, 1, kGlobal, G>(a, b, list, e, end, cut, L); break;
         case 2: r = ws_letter_run<K, 2, kGlobal, G>(a, b, list, e, end, cut, L); break;
@@ -286,8 +288,9 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
         }
     }
     for (uint32_t c = 0; c < n_general; ++c) {
-        const uint32_t s = ld_list<kGlobal>(list + n_single + 2 * c).x;
-        const uint4 M = ld_list<kGlobal>(list + n_single + 2 * c + 1);
+        const uint32_t s = ld_list<kGlobal>(list + n_single + c);  // shift modulo 32
+        const uint4 M = make_uint4(0u - ((s >> 16) & 1u), 0u - ((s >> 17) & 1u), 0u - ((s >> 18) & 1u),
+                                   0u - ((s >> 19) & 1u));
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const uint32_t lo = __funnelshift_r(a[g].x, b[g].x, s);
@@ -508,7 +511,7 @@ template <int VARIANT, int G>
 __device__ __forceinline__ bool tile_first_stage(const uint2 (&a)[G], const uint2 (&b)[G],
                                                  uint32_t tile, const uint32_t (&valid)[G],
                                                  const PatDesc &d, const uint4 *__restrict__ M,
-                                                 uint4 M0, const uint4 *__restrict__ list,
+                                                 uint4 M0, const uint32_t *__restrict__ list,
                                                  const PsConst &pc, const uint2 *__restrict__ planes,
                                                  const uint2 *stage, uint32_t (&pass)[G])
 {

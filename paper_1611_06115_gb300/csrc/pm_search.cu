@@ -207,7 +207,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
         if (it == where.end()) {
             Placed pl{nmask, nmask + pt->nchunks};
             it = where.emplace(pt, pl).first;
-            nmask += pt->nchunks + pt->n_single + 2ull * pt->n_general;
+            nmask += pt->nchunks + wslist_units(pt);
         }
         PatDesc &d = desc[p];
         d.m = pt->m;
@@ -270,7 +270,9 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
         for (const auto &kv : where) {
             const pm_pattern *pt = kv.first;
             std::memcpy(h + kv.second.masks * sizeof(uint4), pt->masks, pt->nchunks * sizeof(uint4));
-            ordered_wslist(pt, text, (uint4 *)(h + kv.second.list * sizeof(uint4)));
+            uint32_t *wl = (uint32_t *)(h + kv.second.list * sizeof(uint4));
+            std::memset(wl, 0, wslist_units(pt) * sizeof(uint4));
+            ordered_wslist(pt, text, wl);
         }
         uint64_t *ht0 = (uint64_t *)(h + nmask * sizeof(uint4));
         for (uint32_t p = 0; p < npat; ++p) ht0[p] = desc[p].tile0;

@@ -9,8 +9,8 @@ depends on the GPU, on k and on the text's statistics.  Two things are tuned:
   lengths over the resident text, and the fastest is installed with
   pm_set_auto_variants;
 * the options of a batched launch (``tune_batch``): the k thresholds between
-  its evaluations, the pairs per work item (patterns per CTA step), the warp
-  tiles per work item (tile width) and the grid, by coordinate descent from
+  its evaluations, the warp tiles per work item (how many tiles a warp walks
+  with one row of pairs loaded) and the grid, by coordinate descent from
   the library's defaults, each candidate timed on a sample of the batch.
 
 Results are cached in a JSON file (``PM_TUNE_CACHE``, default
@@ -43,11 +43,10 @@ BATCH_SPACE = (
     ("ws_below", (1, 3, 5, 7)),
     ("ps1_below", (12, 15, 18, 21, 24)),
     ("ps2_below", (33, 37, 41, 45, 49)),
-    ("group", (8, 16, 64, 256, 1 << 16)),
-    ("tiles", (1, 2, 4)),
+    ("tiles", (2, 4, 8, 16, 32, 64)),
     ("grid", (0,)),  # extended at run time with fractions of the resident grid
 )
-BATCH_DEFAULTS = {"ws_below": 5, "ps1_below": 18, "ps2_below": 41, "group": 16, "tiles": 1, "grid": 0}
+BATCH_DEFAULTS = {"ws_below": 5, "ps1_below": 18, "ps2_below": 41, "tiles": 16, "grid": 0}
 
 
 def valid_variants(k: int) -> list[int]:

@@ -55,7 +55,7 @@ def test_status_codes_instead_of_faults(pm):
         pm.pm_search(t, [p], [-1])
     assert e.value.status == pm.PM_E_ARG
     with pytest.raises(pm.PmError) as e:  # batch option out of range
-        pm.Batch(t, [p], [3], capacity=10, tiles=9)
+        pm.Batch(t, [p], [3], capacity=10, tiles=65)
     assert e.value.status == pm.PM_E_ARG
     with pytest.raises(pm.PmError) as e:  # a symbol outside Table 1
         pm.pm_encode_text(b"ACGTX")

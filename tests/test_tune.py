@@ -68,7 +68,7 @@ def test_select_variants_rejects_invalid_choice():
 
 
 def test_coordinate_descent_finds_separable_minimum():
-    want = {"ws_below": 3, "ps1_below": 21, "ps2_below": 45, "group": 64, "tiles": 2, "grid": 0}
+    want = {"ws_below": 3, "ps1_below": 21, "ps2_below": 45, "tiles": 2, "grid": 0}
     calls = []
 
     def timer(o):
