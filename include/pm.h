@@ -212,7 +212,7 @@ pm_status pm_search(const pm_text *text, const pm_pattern *const *patterns, uint
  *                                        (k <= 63, else ALL_CHUNKS);
  *           PM_VARIANT_WINDOW_SLICED     32 windows per word, bit-sliced
  *                                        counter position by position
- *                                        (k <= 6; larger k run
+ *                                        (k <= 8; larger k run
  *                                        PM_VARIANT_PATTERN_SLICED's rule);
  *           PM_VARIANT_ALL_CHUNKS        one window per word, running
  *                                        counts 32 positions at a time until
@@ -259,7 +259,7 @@ pm_status pm_search_ex(const pm_text *text, const pm_pattern *const *patterns, u
  * table.
  *
  * variant_for_k  nk PM_VARIANT_* values other than AUTO, each valid for its
- *                k (WINDOW_SLICED needs k <= 6, PATTERN_SLICED k <= 31,
+ *                k (WINDOW_SLICED needs k <= 8, PATTERN_SLICED k <= 31,
  *                PATTERN_SLICED_2 k <= 63); read during the call only.
  * nk             0..64; 0 restores the built-in table.  k >= nk uses the
  *                built-in choice (k >= 64 always runs ALL_CHUNKS).  A
@@ -300,7 +300,7 @@ pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
  *                    tiles      warp tiles of 4096 windows per work item,
  *                               1..4 (default 1);
  *                    ws_below   pairs with k < ws_below are evaluated
- *                               window-sliced, 1..7 (default 5; -1: none);
+ *                               window-sliced, 1..9 (default 9; -1: none);
  *                    ps1_below  other pairs with k < ps1_below are evaluated
  *                               pattern-sliced over positions 0..31, then
  *                               settled one window at a time, 1..32

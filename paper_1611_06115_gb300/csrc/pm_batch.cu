@@ -47,7 +47,8 @@ constexpr uint32_t kKindShort = 0;   // pattern-sliced over positions 0..31, sha
 constexpr uint32_t kKindWs = 1;      // window-sliced (k <= kWsMaxK)
 constexpr uint32_t kKindLong = 2;    // pattern-sliced over all chunks (any k)
 constexpr uint32_t kKindShort2 = 3;  // pattern-sliced over positions 0..63, shared shifts (k <= 63)
-// categories of pairs (one launch each): window-sliced with k = 0..kWsMaxK, then these
+// categories of pairs (one launch each): window-sliced with k = 0..kWsMaxK,
+// then these
 constexpr int kCatPs1 = kWsMaxK + 1;
 constexpr int kCatPs2 = kWsMaxK + 2;
 constexpr int kCatLong = kWsMaxK + 3;
@@ -377,8 +378,8 @@ __device__ __forceinline__ void ws_pair(const uint2 (&a)[G], const uint2 (&b)[G]
 
 // CAT: the category of every row of the launch (one launch per category
 // present, so that each kernel carries only its own evaluation: one kernel
-// holding every kind stalled on instruction fetch): 0..kWsMaxK window-sliced
-// pairs with k = CAT, then kCatPs1, kCatPs2, kCatLong.
+// holding every kind stalled on instruction fetch): 0..kWsMaxK
+// window-sliced pairs with k = CAT, then kCatPs1, kCatPs2, kCatLong.
 //
 // A row is one group of up to kP pairs; a work item is a run of T warp
 // tiles crossed with a row, items numbered run-major (item = run * rows +
@@ -554,12 +555,14 @@ const void *batched_kernel(int cat)
     case 4: return batched_ptr<4>();
     case 5: return batched_ptr<5>();
     case 6: return batched_ptr<6>();
+    case 7: return batched_ptr<7>();
+    case 8: return batched_ptr<8>();
     case kCatPs1: return batched_ptr<kCatPs1>();
     case kCatPs2: return batched_ptr<kCatPs2>();
     default: return batched_ptr<kCatLong>();
     }
 }
-static_assert(kWsMaxK == 6, "one window-sliced launch per k = 0 .. 6");
+static_assert(kWsMaxK == 8, "one window-sliced launch per k = 0 .. 8");
 
 // CTAs a launch of category cat keeps resident on the device.
 int batched_grid(int device, int cat)
@@ -587,7 +590,7 @@ struct BatchPlan {
     std::vector<uint4> arena;
     std::vector<uint32_t> order, gkind;
     std::vector<uint2> phases;
-    uint32_t cat_rows[kWsMaxK + 4][2] = {};
+    uint32_t cat_rows[kCats][2] = {};
     int grid = 0;
     uint32_t tiles = 1;
     uint64_t ntiles = 0, runs = 0;
@@ -630,12 +633,12 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
         return PM_E_ARG;
     }
     // Defaults, measured on GB300 (3.1 Gbp text, 64 pairs of m 32..1024):
-    // the window-sliced counter while few positions decide a window (k <= 4),
+    // the window-sliced counters while few positions decide a window (k <= 8),
     // then pattern-sliced groups with shared shifts over one chunk while the
     // windows that survive 32 positions are rare (k <= 17), over two chunks
     // while those surviving 64 are (k <= 40).
     auto below = [](int32_t v, int32_t dflt) { return v == 0 ? dflt : (v < 0 ? 0 : v); };
-    const int ws_max = below(o.ws_below, 5) - 1;  // -1: none
+    const int ws_max = below(o.ws_below, 9) - 1;  // -1: none
     const int ps1_max = below(o.ps1_below, 18) - 1;
     const int ps2_max = below(o.ps2_below, 41) - 1;
     uint32_t tiles = o.tiles > 0 ? (uint32_t)o.tiles : kDefaultTilesPerItem;
@@ -681,19 +684,19 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
     }
     if (arena.empty()) arena.push_back(make_uint4(0, 0, 0, 0));
 
-    // Categories: window-sliced pairs with k = 0, 1, ..., then pattern-sliced
+    // Categories: window-sliced pairs with k = 0, 1, ..., 8, then pattern-sliced
     // pairs over one chunk, over two chunks, and over all chunks.  Within a
     // category pairs are ordered by m and cut into groups of kP, one row
     // each.  A work item is a row crossed with a run of `tiles` warp tiles;
     // each category runs as its own launch, items numbered run-major.
-    std::vector<std::vector<uint32_t>> cats(kWsMaxK + 4);
+    std::vector<std::vector<uint32_t>> cats(kCats);
     for (uint32_t p = 0; p < npat; ++p) {
         const int32_t kp = desc[p].k;
         const Variant v = (Variant)desc[p].variant;
         const size_t c = v == Variant::kWindowSliced    ? (size_t)kp
-                         : v == Variant::kPatternSliced  ? kWsMaxK + 1
-                         : v == Variant::kPatternSliced2 ? kWsMaxK + 2
-                                                         : kWsMaxK + 3;
+                         : v == Variant::kPatternSliced  ? kCatPs1
+                         : v == Variant::kPatternSliced2 ? kCatPs2
+                                                         : kCatLong;
         cats[c].push_back(p);
     }
     // gkind: bits 0-1 the kind, bits 2.. the number of real pairs (the last
@@ -703,9 +706,9 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
         std::vector<uint32_t> &v = cats[c];
         if (v.empty()) continue;
         std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) { return desc[x].m < desc[y].m; });
-        const uint32_t kind = c <= (size_t)kWsMaxK       ? kKindWs
-                              : c == (size_t)kWsMaxK + 1 ? kKindShort
-                              : c == (size_t)kWsMaxK + 2 ? kKindShort2
+        const uint32_t kind = c <= (size_t)kWsMaxK     ? kKindWs
+                              : c == (size_t)kCatPs1 ? kKindShort
+                              : c == (size_t)kCatPs2 ? kKindShort2
                                                          : kKindLong;
         const uint32_t g0 = (uint32_t)pl.gkind.size();
         for (size_t i = 0; i < v.size(); i += kP) {

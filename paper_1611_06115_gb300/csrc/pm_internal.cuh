@@ -131,7 +131,7 @@ constexpr uint32_t kStages = 3;                          // tiles a scan warp ke
 constexpr uint32_t kStageBytes = kStageBlocks * 8;       // one bulk copy per warp tile
 constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
 constexpr uint64_t kWaitLimitNs = 1000000000ull;         // bounded device waits: 1 s
-constexpr int kWsMaxK = 6;                               // window-sliced scan handles k <= 6
+constexpr int kWsMaxK = 8;                               // window-sliced scan handles k <= 8
 constexpr uint64_t kMaxCapacity = 0xffffffffull;         // hits addressable by a tile entry
 
 static_assert(kStageBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
@@ -169,7 +169,7 @@ constexpr uint32_t kDevTimeout = 1u;
 // Scan-kernel variants.
 enum class Variant : int {
     kPatternSliced = 0,   // per window, positions 0..31 in one word, popc; then settle (k <= 31)
-    kWindowSliced = 1,    // per position, 32 windows per word, thermometer counter (k <= 6)
+    kWindowSliced = 1,    // per position, 32 windows per word, bit-sliced counters (k <= 8)
     kPatternSliced2 = 2,  // as kPatternSliced over positions 0..63 (k <= 63)
     kAllChunks = 3,       // per window, running counts over every chunk (any k)
 };

@@ -25,23 +25,31 @@
 //    window has at most k mismatches, and two ALU steps move those four bits
 //    into the lane's pass mask (the word packs windows j, 8+j, 16+j, 24+j,
 //    so each bit lands on its window's own position).  Windows that pass
-//    with m > 32 are settled: counted
-//    one at a time, the first two chunks from the still-staged tile, until
-//    their sum exceeds k or the pattern ends.
+//    with m > 32 are settled.  The first stage may test any full chunk of
+//    the pattern (Eq. 4's sum does not depend on the order of its terms):
+//    the host picks the one with the fewest expected matches for the text.
 //  * pattern-sliced over 64 positions (k <= 63): the same byte test over two
 //    chunks (bit 6), then the same settling.
 //  * every chunk (any k): 32 running counts per lane, chunk after chunk,
 //    until every window of the warp is past k.
-//  * window-sliced (k <= 6): per pattern position j, one word holds the 32
-//    windows' symbols at offset j; a one-letter class gives the mismatch word
-//    in two XOR/OR steps, other classes in three selects, N in none; a
-//    thermometer counter of k+1 words (level i set once a window has more
-//    than i mismatches) adds 32 windows' mismatches at once.  The positions
-//    come from a list built by pm_compile_pattern and ordered for the text
-//    (rarest letters first); each list entry read from shared memory serves
-//    all groups; the warp stops as soon as every window of the tile is past
-//    k (the early stop of Sec. 2.4), or after ws_cut(k) entries, where the
-//    few windows left are counted exactly one by one.
+//  * window-sliced (k <= 8): per pattern position j, one word holds the 32
+//    windows' symbols at offset j.  The positions come from a list built by
+//    pm_compile_pattern and ordered for the text (rarest letters first,
+//    one-letter positions grouped into runs by letter); for a run the
+//    letter's plane (bit set where the text holds that letter) is built once
+//    from the lane's blocks, so a position's match word for 32 windows is one
+//    funnel shift; other classes take three selects.  Mismatches are counted
+//    for 32 windows at once, by a thermometer of k+1 words (k <= 3: level i
+//    set once a window has more than i mismatches) or by six bit-sliced
+//    binary counter words that take four positions per carry-save step (k >=
+//    4, k <= 8).  The warp stops once every window of its tile is past k (k = 0, the
+//    early stop of Sec. 2.4; for larger k a 4096-window tile practically
+//    never dies whole that early) or after a fixed number of list entries;
+//    the windows still alive are then counted exactly.
+//
+// Windows that need exact counts (survivors of a first stage, and every hit)
+// are settled by the whole warp together from a queue in shared memory, and
+// a tile's hits are written once, in window order, behind one atomic.
 //
 // A hit's count is always exact (recounted over every position when the
 // evaluation stopped early for it).
@@ -57,11 +65,13 @@ using namespace scan;
 
 // VARIANT: -1 pattern-sliced over positions 0..31 (k <= 31), -3 over
 // positions 0..63 (k <= 63), -2 pattern-sliced over all chunks (any k); K in
-// 0..kWsMaxK window-sliced with threshold K.  The -2 kernel keeps 32 running
-// counts per lane in registers, so it takes twice the registers at half the
-// resident warps; the window-sliced kernels with K >= 3 keep K+1 counter
-// words per group, the one with K = 0 eight groups per lane (tiles of 8192
-// windows, scan_groups), and run three CTAs per SM.
+// 0..kWsMaxK window-sliced with threshold K, a thermometer counter of K+1
+// words per group below kWsBinaryFrom, five binary counter words from there
+// on.  The -2
+// kernel keeps 32 running counts per lane in registers, so it takes twice
+// the registers at half the resident warps; the window-sliced kernels with
+// K >= 3 and the one with K = 0, which runs eight groups per lane (tiles of
+// 8192 windows, scan_groups), run three CTAs per SM.
 //
 // Each warp stages its tiles kStages strides ahead, one commit group of
 // asynchronous copies per tile (an empty group once the tiles run out, so
@@ -186,7 +196,9 @@ const void *select_kernel(Variant v, int32_t k)
         case 3: return kernel_ptr<3, 4>();
         case 4: return kernel_ptr<4, 4>();
         case 5: return kernel_ptr<5, 4>();
-        default: return kernel_ptr<6, 4>();
+        case 6: return kernel_ptr<6, 4>();
+        case 7: return kernel_ptr<7, 4>();
+        default: return kernel_ptr<8, 4>();
         }
     case Variant::kPatternSliced: return kernel_ptr<-1, 4>();
     case Variant::kPatternSliced2: return kernel_ptr<-3, 4>();
@@ -206,7 +218,7 @@ Variant default_variant(int32_t k)
     // window-sliced counter wins while few positions decide a window, one
     // pattern-sliced chunk while the windows that survive it are rare, two
     // chunks while those surviving 64 positions are rare
-    if (k <= 5) return Variant::kWindowSliced;
+    if (k <= 8) return Variant::kWindowSliced;
     if (k <= 17) return Variant::kPatternSliced;
     if (k <= 40) return Variant::kPatternSliced2;
     return Variant::kAllChunks;

@@ -143,6 +143,9 @@ __device__ __forceinline__ uint32_t ld_list(const uint32_t *p)
 // cost 1.4-4x the scan.
 __host__ __device__ constexpr uint32_t ws_cut(int K) { return K == 0 ? 8u : 4u + 2u * (uint32_t)K; }
 
+// From this K on the window-sliced scan counts in binary (alive_window_sliced_bin).
+constexpr int kWsBinaryFrom = 4;
+
 // Bit i set where symbol i of block t is the letter with Table 1 code CODE
 // (A = 00, C = 01, G = 10, T = 11; t.x holds the low code bits, t.y the high).
 template <int CODE>
@@ -200,9 +203,11 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
         pb[g] = letter_plane<CODE>(b[g]);
     }
     constexpr uint32_t S = K == 0 ? 2u : 4u;
+    // Only k = 0 checks whether every window died: for k >= 1 a tile of
+    // 4096 windows practically never dies whole before the cut.
     auto check = [&]() -> int {
         if (K == 0 && e < 4) return kWsGoOn;
-        if (all_past<K, G>(L)) return kWsDead;
+        if (K == 0 && all_past<K, G>(L)) return kWsDead;
         if (e >= cut) return kWsCut;
         return kWsGoOn;
     };
@@ -244,6 +249,153 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
     return kWsGoOn;
 }
 
+// Binary counters for the window-sliced scan with larger k: per group five
+// bit planes c[0..4] hold, for each of 32 windows, its mismatches so far in
+// binary (c[4] sticky: 16 or more).  Four positions are added at once by
+// carry-save adders (eleven three-input logic operations), so a position
+// costs about 2.75 of them whatever k is, against k+1 for the thermometer.
+// m0..m3 are match words (bit set: the window matches that position); a
+// padding position is all ones.
+constexpr int kCtr = 5;
+__device__ __forceinline__ void add_four(uint32_t (&c)[kCtr], uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3)
+{
+    const uint32_t x0 = ~m0, x1 = ~m1, x2 = ~m2, x3 = ~m3;    // mismatch words
+    const uint32_t s1 = x0 ^ x1 ^ x2;                          // weight 1
+    const uint32_t k1 = (x0 & x1) | (x0 & x2) | (x1 & x2);     // weight 2
+    const uint32_t k2 = (c[0] & s1) | (c[0] & x3) | (s1 & x3); // weight 2
+    c[0] = c[0] ^ s1 ^ x3;
+    const uint32_t k3 = (c[1] & k1) | (c[1] & k2) | (k1 & k2); // weight 4
+    c[1] = c[1] ^ k1 ^ k2;
+    const uint32_t k4 = c[2] & k3;                             // weight 8
+    c[2] ^= k3;
+    const uint32_t k5 = c[3] & k4;                             // weight 16
+    c[3] ^= k4;
+    c[4] |= k5;
+}
+
+// Windows whose count in c is above the compile-time K (K < 16).
+template <int K>
+__device__ __forceinline__ uint32_t count_above(const uint32_t (&c)[kCtr])
+{
+    static_assert(K >= 0 && K < 16, "four counter bits plus the sticky one");
+    uint32_t gt = 0u, eq = kFull;
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        if ((K >> i) & 1) {
+            eq &= c[i];
+        } else {
+            gt |= eq & c[i];
+            eq &= ~c[i];
+        }
+    }
+    return gt | c[4];
+}
+
+// One run of one-letter entries e .. end-1 (letter CODE) added to the binary
+// counters four at a time (the last block of the run padded with matching
+// positions), until `cut` entries are done.
+template <int CODE, bool kGlobal, int G>
+__device__ __forceinline__ int ws_letter_run_bin(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                 const uint32_t *__restrict__ list, uint32_t &e,
+                                                 uint32_t end, uint32_t cut, uint32_t (&C)[G][kCtr])
+{
+    uint32_t pa[G], pb[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        pa[g] = letter_plane<CODE>(a[g]);
+        pb[g] = letter_plane<CODE>(b[g]);
+    }
+    // whole blocks of four, then the run's last block padded with matches
+    while (e + 4 <= end) {
+        uint32_t s[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) s[u] = ld_list<kGlobal>(list + e + u);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            add_four(C[g], __funnelshift_r(pa[g], pb[g], s[0]), __funnelshift_r(pa[g], pb[g], s[1]),
+                     __funnelshift_r(pa[g], pb[g], s[2]), __funnelshift_r(pa[g], pb[g], s[3]));
+        e += 4;
+        if (e >= cut) return kWsCut;  // (no whole-tile early stop: see ws_letter_run)
+    }
+    if (e < end) {
+        const uint32_t left = end - e;  // 1..3
+        const uint32_t s0 = ld_list<kGlobal>(list + e);
+        const uint32_t s1 = left > 1 ? ld_list<kGlobal>(list + e + 1) : 0u;
+        const uint32_t s2 = left > 2 ? ld_list<kGlobal>(list + e + 2) : 0u;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t m1 = __funnelshift_r(pa[g], pb[g], s1), m2 = __funnelshift_r(pa[g], pb[g], s2);
+            add_four(C[g], __funnelshift_r(pa[g], pb[g], s0), left > 1 ? m1 : kFull, left > 2 ? m2 : kFull, kFull);
+        }
+        e = end;
+        if (e >= cut) return kWsCut;
+    }
+    return kWsGoOn;
+}
+
+// The window-sliced first chunk with binary counters, for 4 <= K < 16 (as
+// alive_window_sliced, below, with the thermometer): the listed positions
+// are added four at a time until ws_cut(K) entries are done or the list
+// ends; alive[g] receives the windows still at or below K.  Returns true
+// when it stopped at the cut with some window still alive.
+template <int K, bool kGlobal, int G>
+__device__ __forceinline__ bool alive_window_sliced_bin(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                        const uint32_t *__restrict__ list, uint32_t n_single,
+                                                        uint32_t n_general, uint32_t cut,
+                                                        const uint32_t (&valid)[G], uint32_t (&alive)[G])
+{
+    uint32_t C[G][kCtr];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int i = 0; i < kCtr - 1; ++i) C[g][i] = 0u;
+        C[g][kCtr - 1] = ~valid[g];  // invalid windows count as past every K
+    }
+    uint32_t e = 0;
+    bool stopped = false;
+    while (e < n_single) {
+        const uint32_t h = ld_list<kGlobal>(list + e);
+        const uint32_t he = (h >> 8) & 63u;
+        const uint32_t end = he > e ? (he < n_single ? he : n_single) : e + 1;
+        int r;
+        switch ((h >> 5) & 3u) {
+        case 0: r = ws_letter_run_bin<0, kGlobal, G>(a, b, list, e, end, cut, C); break;
+        case 1: r = ws_letter_run_bin<1, kGlobal, G>(a, b, list, e, end, cut, C); break;
+        case 2: r = ws_letter_run_bin<2, kGlobal, G>(a, b, list, e, end, cut, C); break;
+        default: r = ws_letter_run_bin<3, kGlobal, G>(a, b, list, e, end, cut, C); break;
+        }
+        if (r != kWsGoOn) {
+            stopped = true;
+            break;
+        }
+    }
+    for (uint32_t c = 0; !stopped && c < n_general; c += 4) {
+        const uint32_t left = n_general - c;
+        uint32_t s[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) s[u] = u < left ? ld_list<kGlobal>(list + n_single + c + u) : 0u;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t m[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint4 M = make_uint4(0u - ((s[u] >> 16) & 1u), 0u - ((s[u] >> 17) & 1u),
+                                           0u - ((s[u] >> 18) & 1u), 0u - ((s[u] >> 19) & 1u));
+                m[u] = u < left ? class_match(__funnelshift_r(a[g].x, b[g].x, s[u]),
+                                              __funnelshift_r(a[g].y, b[g].y, s[u]), M)
+                                : kFull;
+            }
+            add_four(C[g], m[0], m[1], m[2], m[3]);
+        }
+        if (n_single + c + 4 >= cut && c + 4 < n_general) stopped = true;
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) alive[g] = ~count_above<K>(C[g]);
+    // (stopped at the cut just as the list ended: alive is exact, and the
+    // caller's settling of it is merely redundant)
+    return stopped;
+}
+
 // Window-sliced first chunk with a thermometer counter of K+1 levels over the
 // listed positions, for all groups of the lane at once.  The list (built by
 // pm_compile_pattern, ordered for the text and packed by ordered_wslist)
@@ -255,12 +407,12 @@ __device__ __forceinline__ int ws_letter_run(const uint2 (&a)[G], const uint2 (&
 // cheaper to count one by one than to carry the whole tile through the
 // remaining positions.  Returns false when every listed position was tested
 // (alive is then exact over the first 32 positions) or every window died.
-template <int K, bool kGlobal = false, int G>
-__device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
-                                                    const uint32_t *__restrict__ list,
-                                                    uint32_t n_single, uint32_t n_general,
-                                                    uint32_t cut, const uint32_t (&valid)[G],
-                                                    uint32_t (&alive)[G])
+template <int K, bool kGlobal, int G>
+__device__ __forceinline__ bool alive_window_sliced_thermo(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                           const uint32_t *__restrict__ list,
+                                                           uint32_t n_single, uint32_t n_general,
+                                                           uint32_t cut, const uint32_t (&valid)[G],
+                                                           uint32_t (&alive)[G])
 {
     uint32_t L[G][K + 1];
 #pragma unroll
@@ -298,7 +450,7 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
             add_position<K>(L[g], class_match(lo, hi, M));
         }
         if ((c & 3) == 3) {
-            if (all_past<K, G>(L)) {
+            if (K == 0 && all_past<K, G>(L)) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) alive[g] = 0u;
                 return false;
@@ -313,6 +465,22 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
 #pragma unroll
     for (int g = 0; g < G; ++g) alive[g] = ~L[g][K];
     return false;
+}
+
+// The window-sliced first chunk: a thermometer counter for K below
+// kWsBinaryFrom (alive_window_sliced_thermo), binary counters from there on
+// (alive_window_sliced_bin).
+template <int K, bool kGlobal = false, int G>
+__device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const uint2 (&b)[G],
+                                                    const uint32_t *__restrict__ list,
+                                                    uint32_t n_single, uint32_t n_general,
+                                                    uint32_t cut, const uint32_t (&valid)[G],
+                                                    uint32_t (&alive)[G])
+{
+    if constexpr (K >= kWsBinaryFrom)
+        return alive_window_sliced_bin<K, kGlobal, G>(a, b, list, n_single, n_general, cut, valid, alive);
+    else
+        return alive_window_sliced_thermo<K, kGlobal, G>(a, b, list, n_single, n_general, cut, valid, alive);
 }
 
 // One warp tile and its halo, global -> shared, completing on bar.

@@ -40,19 +40,19 @@ VARIANT_NAMES = {N.PM_VARIANT_PATTERN_SLICED: "pattern-sliced",
 
 # the batch options tuned, their candidate values, in descent order
 BATCH_SPACE = (
-    ("ws_below", (1, 3, 5, 7)),
+    ("ws_below", (1, 3, 5, 7, 9)),
     ("ps1_below", (12, 15, 18, 21, 24)),
     ("ps2_below", (33, 37, 41, 45, 49)),
     ("tiles", (2, 4, 8, 16, 32, 64)),
     ("grid", (0,)),  # extended at run time with fractions of the resident grid
 )
-BATCH_DEFAULTS = {"ws_below": 5, "ps1_below": 18, "ps2_below": 41, "tiles": 16, "grid": 0}
+BATCH_DEFAULTS = {"ws_below": 9, "ps1_below": 18, "ps2_below": 41, "tiles": 16, "grid": 0}
 
 
 def valid_variants(k: int) -> list[int]:
     """The evaluations that exist at this k (include/pm.h, pm_search_ex)."""
     out = []
-    if k <= 6:
+    if k <= 8:
         out.append(N.PM_VARIANT_WINDOW_SLICED)
     if k <= 31:
         out.append(N.PM_VARIANT_PATTERN_SLICED)

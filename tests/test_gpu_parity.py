@@ -290,7 +290,7 @@ def test_auto_variant_table(pm):
     builtin = pm.pm_get_auto_variants()
     assert len(builtin) == 64
     tables = ([pm.PM_VARIANT_ALL_CHUNKS] * 64,
-              [pm.PM_VARIANT_WINDOW_SLICED if k <= 6 else pm.PM_VARIANT_PATTERN_SLICED_2 for k in range(64)],
+              [pm.PM_VARIANT_WINDOW_SLICED if k <= 8 else pm.PM_VARIANT_PATTERN_SLICED_2 for k in range(64)],
               [pm.PM_VARIANT_PATTERN_SLICED] * 20)
     try:
         for table in tables:
@@ -301,7 +301,7 @@ def test_auto_variant_table(pm):
                 for g, x in zip(got, e):
                     same(g, x)
         before = pm.pm_get_auto_variants()
-        for bad in ([pm.PM_VARIANT_AUTO], [pm.PM_VARIANT_WINDOW_SLICED] * 8, [pm.PM_VARIANT_PATTERN_SLICED] * 33,
+        for bad in ([pm.PM_VARIANT_AUTO], [pm.PM_VARIANT_WINDOW_SLICED] * 10, [pm.PM_VARIANT_PATTERN_SLICED] * 33,
                     [7], [pm.PM_VARIANT_ALL_CHUNKS] * 65):
             with pytest.raises(pm.PmError):
                 pm.pm_set_auto_variants(bad)
@@ -371,3 +371,21 @@ def test_text_save_and_load(pm, tmp_path):
     open(foreign, "wb").write(b"ACGT" * 100)
     with pytest.raises(pm.PmError):
         pm.Text.load(foreign)
+
+
+@pytest.mark.parametrize("k", range(0, 9))
+def test_window_sliced_every_k(pm, k):
+    """The window-sliced evaluation at every k it takes (a thermometer counter
+    below k = 4, carry-save binary counters from k = 4 on), forced for
+    patterns of one to many chunks, with class-heavy first chunks (class
+    positions go through the counters four at a time, runs of one letter
+    end partway through a block of four), over a text of several 8192-window
+    tiles with a ragged tail; element by element against the oracle."""
+    rng = np.random.default_rng(100 + k)
+    text = synth.markov_text(3 * 8192 * 32 + 777, seed=20 + k)
+    t = pm.pm_encode_text(text)
+    pats = [synth.random_pattern(m, nc, rng) for m, nc in ((9, 1), (17, 9), (32, 3), (45, 20), (130, 13))]
+    cps = [pm.pm_compile_pattern(p) for p in pats]
+    r = pm.pm_search_ex(t, cps, [k] * len(cps), variant=pm.PM_VARIANT_WINDOW_SLICED)
+    for i, p in enumerate(pats):
+        same(r.pattern(i), oracle.search(text, p, k))

@@ -16,7 +16,8 @@ class FakeText:
 def test_valid_variants_follow_the_k_limits():
     assert tune.valid_variants(0) == [N.PM_VARIANT_WINDOW_SLICED, N.PM_VARIANT_PATTERN_SLICED,
                                       N.PM_VARIANT_PATTERN_SLICED_2, N.PM_VARIANT_ALL_CHUNKS]
-    assert N.PM_VARIANT_WINDOW_SLICED not in tune.valid_variants(7)
+    assert N.PM_VARIANT_WINDOW_SLICED in tune.valid_variants(8)
+    assert N.PM_VARIANT_WINDOW_SLICED not in tune.valid_variants(9)
     assert tune.valid_variants(32) == [N.PM_VARIANT_PATTERN_SLICED_2, N.PM_VARIANT_ALL_CHUNKS]
     assert tune.valid_variants(64) == [N.PM_VARIANT_ALL_CHUNKS]
 
