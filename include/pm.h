@@ -343,28 +343,32 @@ void pm_batch_free(pm_batch *batch);
  * the method.
  *
  * Who needs it: code that runs where calling the CUDA allocator is not
- * allowed or not wanted, for example inside a host callback, in a
- * real-time loop that may not take the allocator's locks or its implicit
- * synchronisation, or in an application that has already handed all of
- * its device memory to its own allocator.  pm_search draws its scratch from
- * the stream-ordered pool and a pinned host ring; this entry point draws it
- * from one fixed array (about 64 MiB) that the library declares in device
- * global memory.  Every GPU that loads the library holds that array until
- * the process exits.  The call performs no cudaMalloc, cudaMallocAsync,
- * cudaHostAlloc or free of any kind.
+ * allowed or not wanted, for example a real-time loop that may not take the
+ * allocator's locks or its implicit synchronisation, or an application that
+ * has already handed all of its device memory to its own allocator.
+ * pm_search draws its scratch from the stream-ordered pool and a pinned host
+ * ring; this entry point draws it from one fixed array (about 64 MiB) that
+ * the library declares in device global memory.  Every GPU that loads the
+ * library holds that array until the process exits.  The call performs no
+ * cudaMalloc, cudaMallocAsync, cudaHostAlloc or free of any kind.  It does
+ * issue copies, memsets and kernel launches, and waits for the stream when
+ * `needed` is given, so it cannot run where CUDA may not be called at all,
+ * such as inside a host callback (cudaLaunchHostFunc).
  *
  * Arguments are those of pm_search, except that hits and offsets must be
  * device memory (PM_E_ARG otherwise).  Results are identical to pm_search's.
  *
  * Limits (PM_E_TOO_LARGE beyond them, nothing queued): at most 64 (pattern,
  * k) pairs, at most 4096 32-position chunks over the distinct patterns
- * (e.g. m up to 131072 for one pattern), at most 2^21 tiles of 4096 windows
- * over all pairs (e.g. 8.6e9 windows for one pattern), capacity at most
- * 2^22 hits.
+ * (e.g. m up to 131072 for one pattern), at most 2^21 warp tiles over all
+ * pairs (a tile is 4096 windows, 8192 for a window-sliced pair with k = 0;
+ * e.g. 8.6e9 windows for one pattern), capacity at most 2^22 hits.
  *
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture.  All calls share the array and it keeps the
+ * before any stream capture.  The address is kept for the life of the
+ * process, so do not use this entry point on a device after resetting it
+ * (cudaDeviceReset).  All calls share the array and it keeps the
  * previous call's contents (the call clears what has to start at zero):
  * calls whose work overlaps on the GPU, such as calls on two streams or from
  * two threads, race with each other.  Issue them on one stream.

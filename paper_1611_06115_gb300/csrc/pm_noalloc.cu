@@ -1,12 +1,14 @@
 // pm_search_noalloc: the search without any memory allocation.
 //
-// Some callers cannot allocate device memory during a search: code running
-// inside a host callback or a driver thread that must not call into the
-// allocator, applications whose device memory is fully carved up by their own
-// allocator before the search starts, and real-time loops where an
-// allocation (and the implicit synchronisation it may cause) is not allowed.
+// Some callers cannot allocate device memory during a search: applications
+// whose device memory is fully carved up by their own allocator before the
+// search starts, and real-time loops where an allocation (the allocator's
+// locks, and the implicit synchronisation it may cause) is not allowed.
 // pm_search takes its scratch from the stream-ordered pool and a pinned host
-// ring, so it does not suit them.  This entry point runs the same scan and
+// ring, so it does not suit them.  (The call still issues copies, memsets
+// and kernel launches, and waits for the stream when asked for the total,
+// so it is not for code that may not call CUDA at all, such as a host
+// callback.)  This entry point runs the same scan and
 // ordering kernels, but every byte of scratch lives in one fixed array in
 // device global memory that the library declares at file scope.  The array
 // is part of the module: each GPU that loads libpm keeps it until the
@@ -27,10 +29,10 @@ namespace {
 // Limits of this entry point (checked on every call).
 constexpr uint32_t kNaMaxPatterns = 64;            // (pattern, k) pairs per call
 constexpr uint64_t kNaMaxChunks = 4096;            // sum of ceil(m/32) over distinct patterns
-constexpr uint64_t kNaMaxTiles = 1ull << 21;       // sum of ceil((n-m+1)/4096) over the pairs
+constexpr uint64_t kNaMaxTiles = 1ull << 21;       // warp tiles (4096 or 8192 windows) over the pairs
 constexpr uint64_t kNaMaxHits = 1ull << 22;        // capacity
-// arena: chunk masks plus each distinct pattern's window-sliced list (<= 64 entries)
-constexpr uint64_t kNaMaxArena = kNaMaxChunks + 64ull * kNaMaxPatterns;
+// arena: chunk masks plus each distinct pattern's window-sliced list (<= 8 units)
+constexpr uint64_t kNaMaxArena = kNaMaxChunks + 8ull * kNaMaxPatterns;
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffMasks = 0;
@@ -52,6 +54,9 @@ std::mutex g_mu;
 void *g_addr[kMaxDev];
 
 // Once per device, with that device current: look up the array's address.
+// The address is kept for the life of the process; after cudaDeviceReset of
+// a device it no longer holds, so this entry point is not for processes that
+// reset a device and search on it again.
 pm_status scratch_address(int dev, char **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -99,8 +104,13 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
         }
     }
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= kMaxDev || dev != text->device) {
+    pm_status rc0 = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc0) return rc0;
+    if (dev < 0 || dev >= kMaxDev) {
+        set_error("pm_search_noalloc: device %d is beyond this entry point's %d devices", dev, kMaxDev);
+        return PM_E_ARG;
+    }
+    if (dev != text->device) {
         set_error("pm_search_noalloc: text lives on device %d, current device is %d", text->device,
                   dev);
         return PM_E_ARG;

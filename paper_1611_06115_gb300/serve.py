@@ -10,12 +10,15 @@ or one persistent launch for the whole batch (``GpuBackend(batch=...)``).
 
 Memory admission uses a per-query projection of the output size: the
 expected number of windows with at most k mismatches, from a Poisson-
-binomial model of the per-position mismatch probability (letter frequencies
-of a 41 % GC genome; a class position mismatches with the probability of
-the letters outside it), padded by a margin.  A query that still overflows
-its share is re-run alone with its exact count, which the first run reports.
-Latency is completion minus arrival; results are identical to a search of
-the query alone (the kernels are deterministic and queries never interact).
+binomial model of the per-position mismatch probability (the letter
+frequencies the resident text was measured to have when it was coded; a
+class position mismatches with the probability of the letters outside it),
+padded by a margin.  A query that still overflows its share is re-run alone
+with its exact count, which the first run reports.  Latency is completion
+minus arrival, where completion is the moment the query's hits are in the
+caller's memory (host memory with ``GpuBackend(copy_to_host=True)``, the
+device buffers otherwise); results are identical to a search of the query
+alone (the kernels are deterministic and queries never interact).
 
 The backend is pluggable: ``GpuBackend`` issues pm_search_ex calls on the
 slots' streams; tests may drive the scheduling logic with a CPU stand-in.
@@ -29,8 +32,18 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-# letter frequencies of the synthetic genome (A, C, G, T) at 41 % GC
+# letter frequencies (A, C, G, T) assumed when the text's own are not given:
+# a genome at 41 % GC
 LETTER_P = {"A": 0.295, "C": 0.205, "G": 0.205, "T": 0.295}
+
+
+def letter_freqs(counts) -> dict:
+    """Letter frequencies from a text's letter counts (A, C, G, T order, as
+    pm_text_letter_counts gives them)."""
+    tot = float(sum(counts))
+    if tot <= 0:
+        return dict(LETTER_P)
+    return {a: c / tot for a, c in zip("ACGT", counts)}
 CLASS_LETTERS = {
     "A": "A", "C": "C", "G": "G", "T": "T", "M": "AC", "R": "AG", "W": "AT", "S": "CG",
     "Y": "CT", "K": "GT", "V": "ACG", "H": "ACT", "D": "AGT", "B": "CGT", "N": "ACGT",
@@ -55,7 +68,7 @@ def _binomial_head(c: int, q: float, k: int) -> list[float]:
     return out
 
 
-def expected_hits(pattern: str, k: int, n: int) -> float:
+def expected_hits(pattern: str, k: int, n: int, freqs: dict | None = None) -> float:
     """Expected number of windows with at most k mismatches.
 
     The count of a window is a sum of independent per-position mismatch
@@ -64,6 +77,7 @@ def expected_hits(pattern: str, k: int, n: int) -> float:
     convolution of one binomial per class present.  Costs O(classes * k^2)
     instead of O(m * k): it runs once per submitted query, on the host thread
     that also feeds the GPU."""
+    f = freqs or LETTER_P
     m = len(pattern)
     if m > n:
         return 0.0
@@ -71,19 +85,19 @@ def expected_hits(pattern: str, k: int, n: int) -> float:
         return float(n - m + 1)
     dist = [1.0] + [0.0] * k
     for ch, c in collections.Counter(pattern.upper()).items():
-        q = 1.0 - sum(LETTER_P[a] for a in CLASS_LETTERS.get(ch, ""))
+        q = 1.0 - sum(f[a] for a in CLASS_LETTERS.get(ch, ""))
         b = _binomial_head(c, q, k)
         dist = [sum(dist[j] * b[i - j] for j in range(i + 1)) for i in range(k + 1)]
     return float((n - m + 1) * sum(dist))
 
 
-def capacity_for(pattern: str, k: int, n: int) -> int:
+def capacity_for(pattern: str, k: int, n: int, freqs: dict | None = None) -> int:
     """Output records to reserve for one query.  The model ignores the
     text's neighbour correlations (CpG depletion, order-2 context), which
     move short patterns' counts by tens of percent, so the margin is wide:
     device memory is cheaper than re-running a batch whose output did not
     fit."""
-    e = expected_hits(pattern, k, n)
+    e = expected_hits(pattern, k, n, freqs)
     return int(2.0 * e + 16.0 * math.sqrt(e) + 4096)
 
 
@@ -119,9 +133,15 @@ class Server:
     """Continuous-batching scheduler (see the module docstring)."""
 
     def __init__(self, backend, n: int, slots: int = 3, max_batch: int = 64,
-                 mem_budget: int = 8 << 30, clock=time.perf_counter):
+                 mem_budget: int = 8 << 30, clock=time.perf_counter, freqs: dict | None = None):
+        """freqs: the text's letter frequencies for the admission model
+        (default: the backend's ``letter_freqs()`` if it has one, else a
+        genome at 41 % GC)."""
         self.backend = backend
         self.n = n
+        if freqs is None and hasattr(backend, "letter_freqs"):
+            freqs = backend.letter_freqs()
+        self.freqs = freqs
         self.max_batch = max_batch
         self.mem_budget = mem_budget
         self.clock = clock
@@ -145,7 +165,7 @@ class Server:
         """Queue a query.  timeout: seconds after arrival by which it must
         have started, else it expires unanswered."""
         r = Request(self._next, pattern, int(k), self.now() if arrival is None else arrival)
-        r.capacity = capacity_for(pattern, k, self.n)
+        r.capacity = capacity_for(pattern, k, self.n, self.freqs)
         if timeout is not None:
             r.deadline = r.arrival + timeout
         self._next += 1
@@ -296,7 +316,14 @@ class GpuBackend:
     """Issues each batch as one asynchronous pm_search_ex call on its slot's
     stream (device outputs, scratch from the stream-ordered pool): one scan
     launch per query, or with ``batch`` (batch options, {} for defaults) one
-    persistent launch for the whole batch."""
+    persistent launch for the whole batch.
+
+    copy_to_host: deliver each query's hits in pinned host memory.  Once a
+    batch's search has finished its offsets are read and one asynchronous
+    copy of the batch's hits into a pinned buffer is queued on the slot's
+    stream; the batch completes when that copy has landed, so latency
+    includes the copy to the caller.  Otherwise the hits stay on the device
+    and a batch completes with its search."""
 
     def __init__(self, text, slots: int = 3, copy_to_host: bool = False, batch: dict | None = None):
         import torch
@@ -308,6 +335,10 @@ class GpuBackend:
         self.copy_to_host = copy_to_host
         self.batch = batch
         self._compiled: dict[str, object] = {}
+
+    def letter_freqs(self) -> dict:
+        """The resident text's letter frequencies (measured when it was coded)."""
+        return letter_freqs(self.text.letter_counts())
 
     def _pattern(self, p: str):
         c = self._compiled.get(p)
@@ -333,21 +364,44 @@ class GpuBackend:
                                         batch=self.batch)
             ev = torch.cuda.Event()
             ev.record(st)
-        return (res, ev, cap)
+        # [result, search event, capacity, slot, offsets (host), host hits, copy event]
+        return [res, ev, cap, slot, None, None, None]
 
-    @staticmethod
-    def ready(handle) -> bool:
-        return handle[1].query()
+    def ready(self, handle) -> bool:
+        res, ev, cap, slot = handle[0], handle[1], handle[2], handle[3]
+        if not self.copy_to_host:
+            return ev.query()
+        if handle[6] is None:
+            if not ev.query():
+                return False
+            off = res.offsets.cpu().numpy().astype(np.uint64)  # search done: a short copy
+            handle[4] = off
+            total = int(off[-1])
+            if total > cap or total == 0:
+                return True
+            torch = self.torch
+            st = self.streams[slot]
+            host = torch.empty((total, 2), dtype=torch.int32, pin_memory=True)
+            with torch.cuda.stream(st):
+                host.copy_(res.hits[:total], non_blocking=True)
+                cev = torch.cuda.Event()
+                cev.record(st)
+            handle[5], handle[6] = host, cev
+            return False
+        return handle[6].query()
 
     def collect(self, handle, reqs):
-        res, ev, cap = handle
-        off = res.offsets.cpu().numpy().astype(np.uint64)
+        res, cap = handle[0], handle[2]
+        off = handle[4] if handle[4] is not None else res.offsets.cpu().numpy().astype(np.uint64)
         total = int(off[-1])
         counts = [int(off[i + 1] - off[i]) for i in range(len(reqs))]
         if total > cap:
             return counts, [None] * len(reqs)
+        src = handle[5] if self.copy_to_host else res.hits
         out = []
         for i in range(len(reqs)):
-            seg = res.hits[int(off[i]):int(off[i + 1])]
-            out.append(seg.cpu() if self.copy_to_host else seg)
+            if total == 0:
+                out.append(src[0:0] if src is not None else res.hits[0:0].cpu())
+            else:
+                out.append(src[int(off[i]):int(off[i + 1])])
         return counts, out

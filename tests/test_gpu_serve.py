@@ -10,8 +10,9 @@ from synth import workloads
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("batch", (None, {}), ids=("launch-per-query", "one-launch-per-batch"))
-def test_served_results_equal_solo_searches(batch):
+@pytest.mark.parametrize("batch,to_host", ((None, False), ({}, False), (None, True)),
+                         ids=("launch-per-query", "one-launch-per-batch", "hits-to-host"))
+def test_served_results_equal_solo_searches(batch, to_host):
     import torch
     import paper_1611_06115_gb300 as pm
     from paper_1611_06115_gb300 import serve
@@ -21,8 +22,11 @@ def test_served_results_equal_solo_searches(batch):
     # a burst: arrivals outpace the device, so batches queue and overlap
     qs = workloads.serving_queries(rate=20000.0, duration=0.01, seed=32, hi=600)
     queries = [(q.arrival, q.pattern, q.k) for q in qs]
-    backend = serve.GpuBackend(text, slots=3, batch=batch)
+    backend = serve.GpuBackend(text, slots=3, batch=batch, copy_to_host=to_host)
     srv = serve.Server(backend, n=text.n, slots=3, max_batch=8, mem_budget=4 << 30)
+    # admission sizes outputs with the text's own letter frequencies
+    counts = text.letter_counts()
+    assert srv.freqs == serve.letter_freqs(counts) and abs(sum(srv.freqs.values()) - 1) < 1e-12
     stats = serve.run_trace(srv, queries)
     torch.cuda.synchronize()
     assert stats["completed"] == len(queries)
@@ -31,6 +35,7 @@ def test_served_results_equal_solo_searches(batch):
     for r in srv.done:
         cp = by_pattern.setdefault(r.pattern, pm.pm_compile_pattern(r.pattern))
         alone = pm.pm_search(text, [cp], [r.k]).pattern(0)
+        assert (r.hits.device.type == "cpu") == to_host
         got = r.hits.cpu().numpy().view(np.uint32).reshape(-1, 2)
         assert r.count == alone[0].size
         assert np.array_equal(got[:, 0], alone[0]) and np.array_equal(got[:, 1], alone[1])

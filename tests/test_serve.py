@@ -178,3 +178,23 @@ def test_queries_past_their_deadline_expire_unstarted():
     assert len(srv.expired) > 0 and len(srv.done) + len(srv.expired) == 8
     assert all(r.qid not in launched and r.status == "expired" for r in srv.expired)
     assert all(r.status == "done" for r in srv.done)
+
+
+def test_expected_hits_takes_the_text_letter_frequencies():
+    """The admission model uses the frequencies it is given: a text of only
+    A and T makes a C or G position mismatch every window, and the
+    frequencies come from letter counts in Table 1 order."""
+    n = 10_000
+    f = serve.letter_freqs([500, 0, 0, 500])
+    assert f == {"A": 0.5, "C": 0.0, "G": 0.0, "T": 0.5}
+    assert serve.expected_hits("C", 0, n, f) == 0.0
+    assert abs(serve.expected_hits("A", 0, n, f) - 0.5 * n) < 1e-9 * n
+    assert abs(serve.expected_hits("W", 0, n, f) - n) < 1e-9 * n   # W = A or T
+    assert serve.letter_freqs([0, 0, 0, 0]) == serve.LETTER_P
+    # the server takes the backend's frequencies for its capacities
+    class B:
+        def letter_freqs(self):
+            return f
+    srv = serve.Server(B(), n=n)
+    r = srv.submit("SSSS", 0)   # S = C or G: never matches this text
+    assert srv.freqs is f and r.capacity == serve.capacity_for("SSSS", 0, n, f) == 4096
