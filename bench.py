@@ -54,8 +54,8 @@ VARIANT_NAMES = {1: "pattern-sliced", 2: "window-sliced", 3: "pattern-sliced-64"
 # the hash (kernel_source_sha) of the scan kernel's sources at capture time,
 # and the line reports no traffic when the sources no longer match.
 TRAFFIC_KERNEL = "k_scan<pattern-sliced>"
-TRAFFIC_BYTES_8E8 = None
-TRAFFIC_SRC_SHA = None
+TRAFFIC_BYTES_8E8 = (200.080384 + 0.850176) * 1e6
+TRAFFIC_SRC_SHA = "33a802b64d163b86"
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, k = 16 m = 128 launch at "
                   "n = 8e8 (profiles/k_scan_genome_ncu_800M.md), scaled by windows")
 KERNEL_SOURCES = ("pm_scan.cu", "pm_scan_impl.cuh", "pm_internal.cuh")
@@ -832,7 +832,7 @@ def run_large(a):
 def run_profile(a):
     """Five single searches of the GENOME m = 128 pattern over the first n
     symbols, one per kernel kind, for a small ncu capture:
-    (pattern-sliced, k = 4), (window-sliced, 0), (window-sliced, 4),
+    (window-sliced, k = 0), (window-sliced, 4), (window-sliced, 8),
     (pattern-sliced, 16), (pattern-sliced over 64 positions, 24)."""
     import torch
     import paper_1611_06115_gb300 as pm
@@ -841,7 +841,7 @@ def run_profile(a):
     build_text(a.n, 0, host.numpy(), pats)
     text = pm.pm_encode_text(host)
     c = pm.pm_compile_pattern(pats[1])
-    for v, k in ((1, 4), (2, 0), (2, 4), (1, 16), (3, 24)):
+    for v, k in ((2, 0), (2, 4), (2, 8), (1, 16), (3, 24)):
         r = pm.pm_search_ex(text, [c], [k], variant=v)
         print(json.dumps({"variant": v, "k": k, "hits": r.total}), flush=True)
 
