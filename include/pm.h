@@ -189,7 +189,9 @@ void pm_pattern_free(pm_pattern *pattern);
  *
  * If the total exceeds capacity, offsets still hold every pattern's count
  * and no hit record is written.  A device-side failure makes offsets[npat]
- * equal PM_TOTAL_ERROR (and the synchronous forms return PM_E_TIMEOUT).
+ * equal PM_TOTAL_ERROR (and the synchronous forms return PM_E_TIMEOUT); the
+ * present search kernels have no bounded wait that could raise it, and
+ * callers still check for it.
  * Scratch memory is taken from the stream-ordered pool of the current
  * device (cudaMallocAsync) and released on the stream before returning.
  */
@@ -381,14 +383,17 @@ pm_status pm_search_noalloc(const pm_text *text, const pm_pattern *const *patter
 
 /*
  * pm_check_bounded_wait -- failure detection, checked without a fault.  The
- * paper has no counterpart.  Every wait of the scan kernels on a bulk copy
- * gives up after a time limit (1 s in the kernels), sets a status bit and
- * returns, so a lost copy ends as PM_E_TIMEOUT instead of a hung GPU.  This
- * entry point runs that same bounded wait once, in a one-warp kernel, on a
- * barrier that receives its arrival only if `arrive` is nonzero, with the
- * given limit (1 ns .. 10 s; PM_E_ARG otherwise), and reports through
- * *timed_out whether the wait gave up (1) or completed (0).  Nothing is left
- * pending on the device either way.
+ * paper has no counterpart.  The search kernels hold no spin wait: their
+ * copies are per-lane cp.async, completed by cp.async.wait_group.  Any
+ * kernel of this library that waits on a shared-memory barrier (an mbarrier
+ * completed by a bulk copy) must use the bounded form, which gives up after
+ * a time limit, sets the device status bit that turns offsets[npat] into
+ * PM_TOTAL_ERROR, and returns, so a lost copy ends as PM_E_TIMEOUT instead
+ * of a hung GPU.  This entry point runs that bounded wait once, in a
+ * one-warp kernel, on a barrier that receives its arrival only if `arrive`
+ * is nonzero, with the given limit (1 ns .. 10 s; PM_E_ARG otherwise), and
+ * reports through *timed_out whether the wait gave up (1) or completed (0).
+ * Nothing is left pending on the device either way.
  */
 pm_status pm_check_bounded_wait(uint64_t limit_ns, int32_t arrive, uint32_t *timed_out);
 

@@ -125,16 +125,10 @@ constexpr int kScanThreads = 256;                        // threads per scan CTA
 constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kGroups = 4;                               // 32-window groups per lane per tile
 constexpr uint64_t kTileWindows = 32ull * 32 * kGroups;  // one warp tile: 4096 windows
-constexpr int kStageBlocks = 32 * kGroups + 2;           // a warp tile's blocks + 2 halo blocks
-constexpr int kScanStageBlocks = kStageBlocks + 2;       // per-pattern scan: from an even block
 constexpr uint32_t kStages = 3;                          // tiles a scan warp keeps staged or in flight
-constexpr uint32_t kStageBytes = kStageBlocks * 8;       // one bulk copy per warp tile
 constexpr uint64_t kPadBlocks = 1024;                    // zero blocks after the text
-constexpr uint64_t kWaitLimitNs = 1000000000ull;         // bounded device waits: 1 s
 constexpr int kWsMaxK = 8;                               // window-sliced scan handles k <= 8
 constexpr uint64_t kMaxCapacity = 0xffffffffull;         // hits addressable by a tile entry
-
-static_assert(kStageBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // One (pattern, k) of a search, as the kernels see it.
 struct PatDesc {
@@ -338,17 +332,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// A 16-byte shared-memory load the compiler may not hoist out of a loop
-// (keeps loop-invariant masks out of registers where they would spill).
-__device__ __forceinline__ uint4 lds_u4(const uint4 *p)
-{
-    uint4 r;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "r"(smem_u32(p)));
-    return r;
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
@@ -360,29 +343,11 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Orders this thread's earlier generic-proxy accesses to shared memory before
-// later async-proxy (bulk copy) accesses.
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-
-// Bulk (TMA) copy global -> shared, completing on an mbarrier.  Both
-// addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -141,9 +141,10 @@ using namespace pm;
 namespace pm {
 namespace {
 
-// The bounded barrier wait every scan kernel uses on its bulk copies, on a
-// barrier that receives its one arrival only if `arrive` is set: without it
-// nothing completes the phase and the wait must give up after limit_ns.
+// The bounded barrier wait that any kernel waiting on an mbarrier (a bulk
+// copy's completion) must use, on a barrier that receives its one arrival
+// only if `arrive` is set: without it nothing completes the phase and the
+// wait must give up after limit_ns.
 // out[0] = 1 when the wait gave up, out[1] = 1 once the kernel returned.
 __global__ void k_bounded_wait(uint64_t limit_ns, int arrive, uint32_t *out)
 {

@@ -483,14 +483,6 @@ __device__ __forceinline__ bool alive_window_sliced(const uint2 (&a)[G], const u
         return alive_window_sliced_thermo<K, kGlobal, G>(a, b, list, n_single, n_general, cut, valid, alive);
 }
 
-// One warp tile and its halo, global -> shared, completing on bar.
-__device__ __forceinline__ void issue_tile(const uint2 *planes, uint64_t tile, uint2 *dst,
-                                           uint64_t *bar)
-{
-    dev::mbar_arrive_expect_tx(bar, kStageBytes);
-    dev::bulk_g2s(dst, planes + tile * (32ull * G), kStageBytes, bar);
-}
-
 // Blocks a per-pattern scan stage holds: a warp tile of 32G blocks from an
 // even block (the one at or below the tile's first block plus the first-stage
 // chunk), the 2-block halo, and one more block so that the count is even.

@@ -1,7 +1,7 @@
-"""Failure detection without a GPU fault: the bounded barrier wait every
-scan kernel uses on its bulk copies gives up after its limit when nothing
-completes the barrier, the kernel returns, and the context stays usable;
-capacity overflows and bad arguments come back as status codes."""
+"""Failure detection without a GPU fault: the bounded barrier wait that any
+kernel waiting on a bulk copy's barrier uses gives up after its limit when
+nothing completes the barrier, the kernel returns, and the context stays
+usable; capacity overflows and bad arguments come back as status codes."""
 import time
 
 import numpy as np
