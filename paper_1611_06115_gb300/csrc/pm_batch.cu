@@ -1,24 +1,25 @@
 // Batched search: many patterns of uneven m and k in one persistent launch
-// over the resident text.
+// per category of evaluation over the resident text.
 //
 // The planner sorts the (pattern, k) pairs into categories by evaluation
-// (window-sliced per k, pattern-sliced over 32 positions, over 64 positions,
-// every chunk; thresholds are options), orders each category by m and cuts
-// it into groups of kP pairs; a row holds the groups of one category (all
-// of them unless the options cut it shorter).  A work item is a row crossed
-// with a run of warp tiles; rows are outermost, so all warps run one kind of
-// evaluation at a time, and each tile is staged once for every pair of its
-// row: the text is read from device memory once per row.  A warp stages its
-// tiles (plus halo) in shared memory by its lanes' own asynchronous copies
-// kStages tiles ahead, then per group of the row
-//   * pattern-sliced group: for each window, the funnel shifts that line the
+// (window-sliced for each k, pattern-sliced over 32 positions, over 64
+// positions, every chunk; thresholds are options), orders each category by m
+// and cuts it into rows of up to kP pairs.  Each category present gets its
+// own launch, so every kernel carries only its own evaluation.  A work item
+// is a row crossed with a run of warp tiles, items numbered run-major: the
+// warps at work at any time cover a few runs of tiles with every row, so a
+// tile comes from device memory once per launch and from L2 for the other
+// rows.  A warp stages its tiles (plus halo) in shared memory by its lanes'
+// own asynchronous copies kStages tiles ahead, loads its item's row into
+// shared memory once, then per tile
+//   * pattern-sliced row: for each window, the funnel shifts that line the
 //     text up with the first 32 (or 64) positions are done once and serve
-//     every pair of the group (whose masks sit in shared memory), so a
+//     every pair of the row (whose masks sit in shared memory), so a
 //     pair-window costs three (or six) selects, one (or two) popcounts and a
 //     quarter of the byte-packed threshold test;
-//   * window-sliced group: each pair copies its position list to shared
-//     memory and runs the letter-plane thermometer scan over the tile;
-//   * every-chunk group: each pair keeps 32 running counts per lane.
+//   * window-sliced row: each pair runs the letter-plane scan over the tile
+//     from its compact position list in shared memory;
+//   * every-chunk row: each pair keeps 32 running counts per lane.
 // The candidates of a pair in a tile (or a 1024-window group of it) are
 // settled by the whole warp from a shared-memory queue; their hits are
 // written contiguously, in window order, behind one warp-aggregated atomic,
@@ -260,17 +261,17 @@ __device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], u
 
 // One pattern-sliced group over the first C chunks (C = 1: k <= 31, C = 2:
 // k <= 63) on one staged tile: for each window the funnel shifts that line
-// the text up with the chunks are done once and serve all kP pairs of the
+// the text up with the chunks are done once and serve all kP slots of the
 // group, whose masks sit in shared memory (sM0, sM1; sP {k in every byte};
-// loaded once per work item).  Bytes of the multiply-add results hold
-// (4/C) * (matches + k) <= (4/C) * (64C - 1) < 256, so bit 7 of a byte is set
-// exactly when matches + k >= 32C, i.e. when the window has at most k
-// mismatches in those positions.  The candidates of each pair and group are
-// then settled by the warp together (settle_emit_record; each lane its own
-// when there are too many).
-// kAll: all kP slots hold pairs (every group but the last of a category);
-// otherwise the empty slots are skipped.
-template <int C, bool kAll>
+// loaded once per work item; a slot without a pair has empty masks and
+// k = 0, so none of its windows ever passes).  Bytes of the multiply-add
+// results hold (4/C) * (matches + k) <= (4/C) * (64C - 1) < 256, so bit 7 of
+// a byte is set exactly when matches + k >= 32C, i.e. when the window has at
+// most k mismatches in those positions.  Candidates are rare: one settling
+// loop over the pairs (not unrolled, so the kernel carries that code once)
+// settles each pair's candidates with the whole warp (settle_emit_record;
+// each lane its own when there are too many).
+template <int C>
 __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t cnt, const RowPair *rp,
                                             const uint4 *sM0, const uint4 *sM1, const uint4 *sP, uint32_t *q,
                                             uint32_t two, const BatchArgs &ba)
@@ -279,7 +280,6 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
     const uint32_t m1 = C == 1 ? two << 1 : two, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
-        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
         const uint2 ta = stage[32 * g + lane], tb = stage[32 * g + lane + 1];
         const uint2 c = C == 2 ? stage[32 * g + lane + 2] : make_uint2(0u, 0u);
         uint32_t acc[kP];
@@ -301,7 +301,6 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
             }
 #pragma unroll
             for (int p = 0; p < kP; ++p) {
-                if (!kAll && p >= (int)cnt) break;  // warp-uniform
                 const uint4 M0 = sM0[p];
                 uint32_t gm[4];
 #pragma unroll
@@ -319,22 +318,28 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 acc[p] |= (v >> (7 - j)) & (0x01010101u << j);
             }
         }
+        uint32_t anyp = 0;
 #pragma unroll
-        for (int p = 0; p < kP; ++p) {
-            if (p < (int)cnt) {
-                const RowPair &r = rp[p];
-                if (tile >= r.ntiles) continue;
-                uint32_t pass[1] = {acc[p] & pair_valid(r, tile, blk)};
-                if (!__any_sync(kFull, pass[0] != 0u)) continue;
-                if (!settle_emit_record<1>(pass, (uint32_t)g, tile, stage, q, r, ba)) {
-                    const uint4 *M = ba.arena + r.masks;
-                    if (r.nchunks > (uint32_t)C)
-                        pass[0] = settle_staged(pass[0], blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, r.nchunks,
-                                                r.k, ba.planes);
-                    if (__any_sync(kFull, pass[0] != 0u))
-                        emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
-                                   r.nchunks, r.k, M, ba);
-                }
+        for (int p = 0; p < kP; ++p) anyp |= acc[p];
+        if (!__any_sync(kFull, anyp != 0u)) continue;  // warp-uniform; the common case
+        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+#pragma unroll 1
+        for (uint32_t p = 0; p < cnt; ++p) {
+            const RowPair &r = rp[p];
+            if (tile >= r.ntiles) continue;
+            uint32_t a = acc[0];  // acc[p] by selects: a run-time index would move acc to local memory
+#pragma unroll
+            for (uint32_t i = 1; i < (uint32_t)kP; ++i) a = p == i ? acc[i] : a;
+            uint32_t pass[1] = {a & pair_valid(r, tile, blk)};
+            if (!__any_sync(kFull, pass[0] != 0u)) continue;
+            if (!settle_emit_record<1>(pass, (uint32_t)g, tile, stage, q, r, ba)) {
+                const uint4 *M = ba.arena + r.masks;
+                if (r.nchunks > (uint32_t)C)
+                    pass[0] = settle_staged(pass[0], blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, r.nchunks, r.k,
+                                            ba.planes);
+                if (__any_sync(kFull, pass[0] != 0u))
+                    emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g, r.nchunks,
+                               r.k, M, ba);
             }
         }
     }
@@ -437,6 +442,13 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
         const uint32_t grp = ph.x;
         const uint32_t cnt = __ldg(ba.gkind + grp) >> 2;
         __syncwarp();  // the previous item is done with the row's slots
+        if constexpr (!kWsCat) {
+            if (lane >= (int)cnt && lane < kP) {  // empty slot: no position matches, k = 0
+                sM0[warp][lane] = make_uint4(0u, 0u, 0u, 0u);
+                sM1[warp][lane] = make_uint4(0u, 0u, 0u, 0u);
+                sP[warp][lane] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
         if (lane < (int)cnt) {
             const uint32_t p = __ldg(ba.order + grp * kP + lane);
             const PatDesc &d = ba.pats[p];
@@ -512,12 +524,8 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
                     }
                 } else {
                     constexpr int C = CAT == kCatPs1 ? 1 : 2;
-                    if (cnt == kP)
-                        short_group<C, true>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp],
-                                             squeue[warp], two, ba);
-                    else
-                        short_group<C, false>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp],
-                                              squeue[warp], two, ba);
+                    short_group<C>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp], squeue[warp],
+                                   two, ba);
                 }
             }
             // refill this stage with the position S ahead
