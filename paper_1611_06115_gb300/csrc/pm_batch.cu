@@ -43,6 +43,7 @@
 namespace pm {
 namespace {
 constexpr int kP = 8;  // pairs per group
+constexpr uint32_t kSpassWords = kP * scan::G * 32;  // pass words of one pattern-sliced row and tile
 // group kinds
 constexpr uint32_t kKindShort = 0;   // pattern-sliced over positions 0..31, shared shifts (k <= 31)
 constexpr uint32_t kKindWs = 1;      // window-sliced (k <= kWsMaxK)
@@ -267,17 +268,21 @@ __device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], u
 // k = 0, so none of its windows ever passes).  Bytes of the multiply-add
 // results hold (4/C) * (matches + k) <= (4/C) * (64C - 1) < 256, so bit 7 of
 // a byte is set exactly when matches + k >= 32C, i.e. when the window has at
-// most k mismatches in those positions.  Candidates are rare: one settling
-// loop over the pairs (not unrolled, so the kernel carries that code once)
-// settles each pair's candidates with the whole warp (settle_emit_record;
-// each lane its own when there are too many).
+// most k mismatches in those positions.  The pass words of every slot and
+// group go to shared memory (spass); once the tile is done, one loop over the
+// pairs (not unrolled, so the kernel carries that code once) settles each
+// pair's candidates of the whole tile together with the whole warp
+// (settle_emit_record; each lane its own when there are too many).  A
+// 1024-window group holds about two candidates of a pair on the 4096-pattern
+// workload, so settling per group cost as much as the evaluation.
 template <int C>
 __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, uint32_t cnt, const RowPair *rp,
                                             const uint4 *sM0, const uint4 *sM1, const uint4 *sP, uint32_t *q,
-                                            uint32_t two, const BatchArgs &ba)
+                                            uint32_t *spass, uint32_t two, const BatchArgs &ba)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t m1 = C == 1 ? two << 1 : two, m8 = m1 << 8, m16 = m1 << 16, m24 = m1 << 24;
+    uint32_t anyp = 0;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
         const uint2 ta = stage[32 * g + lane], tb = stage[32 * g + lane + 1];
@@ -318,31 +323,43 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 acc[p] |= (v >> (7 - j)) & (0x01010101u << j);
             }
         }
-        uint32_t anyp = 0;
 #pragma unroll
-        for (int p = 0; p < kP; ++p) anyp |= acc[p];
-        if (!__any_sync(kFull, anyp != 0u)) continue;  // warp-uniform; the common case
-        const uint64_t blk = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
-#pragma unroll 1
-        for (uint32_t p = 0; p < cnt; ++p) {
-            const RowPair &r = rp[p];
-            if (tile >= r.ntiles) continue;
-            uint32_t a = acc[0];  // acc[p] by selects: a run-time index would move acc to local memory
-#pragma unroll
-            for (uint32_t i = 1; i < (uint32_t)kP; ++i) a = p == i ? acc[i] : a;
-            uint32_t pass[1] = {a & pair_valid(r, tile, blk)};
-            if (!__any_sync(kFull, pass[0] != 0u)) continue;
-            if (!settle_emit_record<1>(pass, (uint32_t)g, tile, stage, q, r, ba)) {
-                const uint4 *M = ba.arena + r.masks;
-                if (r.nchunks > (uint32_t)C)
-                    pass[0] = settle_staged(pass[0], blk, ta, tb, stage + 32 * g + lane + 2, M, 0u, r.nchunks, r.k,
-                                            ba.planes);
-                if (__any_sync(kFull, pass[0] != 0u))
-                    emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g, r.nchunks,
-                               r.k, M, ba);
-            }
+        for (int p = 0; p < kP; ++p) {
+            spass[(p * G + g) * 32 + lane] = acc[p];
+            anyp |= acc[p];
         }
     }
+    if (!__any_sync(kFull, anyp != 0u)) return;  // warp-uniform; the common case
+    __syncwarp();
+    uint64_t blk[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+#pragma unroll 1
+    for (uint32_t p = 0; p < cnt; ++p) {
+        const RowPair &r = rp[p];
+        if (tile >= r.ntiles) continue;
+        uint32_t pass[G], anyr = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            pass[g] = spass[(p * G + g) * 32 + lane] & pair_valid(r, tile, blk[g]);
+            anyr |= pass[g];
+        }
+        if (!__any_sync(kFull, anyr != 0u) || settle_emit_record<G>(pass, 0u, tile, stage, q, r, ba)) continue;
+        const uint4 *M = ba.arena + r.masks;
+#pragma unroll 1
+        for (int g = 0; g < G; ++g) {
+            uint32_t ps = pass[0];  // pass[g] by selects (a run-time index would move pass to local memory)
+#pragma unroll
+            for (int i = 1; i < G; ++i) ps = g == i ? pass[i] : ps;
+            if (r.nchunks > (uint32_t)C)
+                ps = settle_staged(ps, blk[0] + 32ull * g, stage[32 * g + lane], stage[32 * g + lane + 1],
+                                   stage + 32 * g + lane + 2, M, 0u, r.nchunks, r.k, ba.planes);
+            if (__any_sync(kFull, ps != 0u))
+                emit_group(ps, blk[0] + 32ull * g, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
+                           r.nchunks, r.k, M, ba);
+        }
+    }
+    __syncwarp();  // spass is rewritten by the next tile
 }
 
 // Window-sliced pair rp over one staged tile (a, b: the lane's blocks; list:
@@ -408,6 +425,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
     __shared__ uint4 sM0[kScanWarps][kP];
     __shared__ uint4 sM1[kScanWarps][kP];
     __shared__ uint4 sP[kScanWarps][kP];  // pattern-sliced group: {k in every byte, 0, 0, 0}
+    extern __shared__ uint32_t spass[];  // pattern-sliced row: its pass words, kSpassWords per warp
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -525,7 +543,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
                 } else {
                     constexpr int C = CAT == kCatPs1 ? 1 : 2;
                     short_group<C>(stage, tile, cnt, srow[warp], sM0[warp], sM1[warp], sP[warp], squeue[warp],
-                                   two, ba);
+                                   spass + warp * kSpassWords, two, ba);
                 }
             }
             // refill this stage with the position S ahead
@@ -572,15 +590,31 @@ const void *batched_kernel(int cat)
 }
 static_assert(kWsMaxK == 8, "one window-sliced launch per k = 0 .. 8");
 
-// CTAs a launch of category cat keeps resident on the device.
+// Dynamic shared memory of a launch of category cat: the pass words of a
+// pattern-sliced row (with the static arrays past the 48 KB that static
+// shared memory may hold).
+size_t batched_smem(int cat)
+{
+    return cat == kCatPs1 || cat == kCatPs2 ? (size_t)kScanWarps * kSpassWords * sizeof(uint32_t) : 0;
+}
+
+// Sets the kernel of category cat up on the current device (its dynamic
+// shared memory limit) and returns how many CTAs a launch keeps resident
+// (0 on failure, with the error left for cudaGetLastError).
 int batched_grid(int device, int cat)
 {
-    static std::atomic<int> cache[64][kCats];  // 0 = not yet computed
+    static std::atomic<int> cache[64][kCats];  // 0 = not yet set up
     if (device < 0 || device >= 64 || cat < 0 || cat >= kCats) return 0;
     if (const int g = cache[device][cat].load(std::memory_order_relaxed)) return g;
     int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(cat), kScanThreads, 0);
+    const size_t smem = batched_smem(cat);
+    if (smem && cudaFuncSetAttribute(batched_kernel(cat), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(cat), kScanThreads, smem) !=
+            cudaSuccess)
+        return 0;
     const int g = sms * (per_sm < 1 ? 1 : per_sm);
     cache[device][cat].store(g, std::memory_order_relaxed);
     return g;
@@ -841,11 +875,17 @@ pm_status run_batch(const pm_batch *b, pm_hit *hits, uint64_t *offsets, cudaStre
                      b->tmp,    b->capacity, cursor,  b->recs,  b->capacity, rec_cursor,
                      b->pat_counts, status};
         uint64_t grid = (items + kScanWarps - 1) / kScanWarps;
-        const int lim = b->grid > 0 ? b->grid : batched_grid(b->device, cat);
+        const int resident = batched_grid(b->device, cat);
+        if (resident == 0) {
+            rc = cuda_status(cudaGetLastError(), "batched kernel set-up");
+            if (!rc) rc = cuda_status(cudaErrorInvalidValue, "batched kernel set-up");
+            break;
+        }
+        const int lim = b->grid > 0 ? b->grid : resident;
         if (grid > (uint64_t)lim) grid = (uint64_t)lim;
         void *args[] = {(void *)&ba};
-        rc = cuda_status(cudaLaunchKernel(batched_kernel(cat), dim3((unsigned)grid), dim3(kScanThreads), args, 0,
-                                          st),
+        rc = cuda_status(cudaLaunchKernel(batched_kernel(cat), dim3((unsigned)grid), dim3(kScanThreads), args,
+                                          batched_smem(cat), st),
                          "batched scan kernel");
     }
     SegRecord *sorted = b->recs;
@@ -911,6 +951,13 @@ pm_status pm_batch_create(const pm_text *text, const pm_pattern *const *patterns
     BatchPlan pl;
     rc = plan_batch("pm_batch_create", text, patterns, npat, k, opts, dev, pl);
     if (rc) return rc;
+    // the kernels' set-up on this device happens here, before any launch
+    // (and before a stream capture of pm_batch_run)
+    for (int cat = 0; cat < kCats; ++cat)
+        if (pl.cat_rows[cat][1] > pl.cat_rows[cat][0] && batched_grid(dev, cat) == 0) {
+            rc = cuda_status(cudaGetLastError(), "batched kernel set-up");
+            return rc ? rc : cuda_status(cudaErrorInvalidValue, "batched kernel set-up");
+        }
     cudaStream_t st = (cudaStream_t)stream;
     pm_batch *b = new (std::nothrow) pm_batch{};
     if (!b) return PM_E_NOMEM;
