@@ -194,11 +194,14 @@ int scan_grid_limit(Variant v, int32_t k, int device);
 Variant auto_variant(const PatDesc &d, int device);
 
 // 32-window groups per lane in a warp tile of the per-pattern scan kernel of
-// variant v (resolved) at this k: 8 for the window-sliced kernel with k = 0,
-// whose evaluation per tile is short enough that the per-tile work (copies,
-// list reads, early-stop checks) weighs, else 4.  A tile covers
+// variant v (resolved) at this k: 8 for the window-sliced kernels, whose
+// evaluation per tile is short enough that the per-tile work (copies, list
+// reads, checks, the tile's entry) weighs (GB300, 3.1 Gbp, against 4: k = 1
+// 0.31 -> 0.27 ms, k = 2 0.47 -> 0.41 ms, k = 4 0.64 -> 0.61 ms, k = 8
+// 0.84 -> 0.82 ms; from k = 3 on with half the resident warps, so that the
+// counters of eight groups stay in registers), else 4.  A tile covers
 // 1024 * scan_groups windows.
-inline int scan_groups(Variant v, int32_t k) { return v == Variant::kWindowSliced && k == 0 ? 8 : 4; }
+inline int scan_groups(Variant v, int32_t) { return v == Variant::kWindowSliced ? 8 : 4; }
 inline uint64_t scan_tile_windows(Variant v, int32_t k) { return 1024ull * (uint64_t)scan_groups(v, k); }
 
 // PM_VARIANT_* (not AUTO) <-> Variant.

@@ -69,9 +69,10 @@ using namespace scan;
 // words per group below kWsBinaryFrom, five binary counter words from there
 // on.  The -2
 // kernel keeps 32 running counts per lane in registers, so it takes twice
-// the registers at half the resident warps; the window-sliced kernels with
-// K >= 3 and the one with K = 0, which runs eight groups per lane (tiles of
-// 8192 windows, scan_groups), run three CTAs per SM.
+// the registers at half the resident warps.  The window-sliced kernels run
+// eight groups per lane (tiles of 8192 windows, scan_groups): three CTAs per
+// SM for K <= 2, two from K = 3 on (the counters of eight groups take up to
+// 128 registers).
 //
 // Each warp stages its tiles kStages strides ahead, one commit group of
 // asynchronous copies per tile (an empty group once the tiles run out, so
@@ -79,7 +80,7 @@ using namespace scan;
 // once its tile is done (settling and hit counts read the staged tile).
 // Tile indices fit in 32 bits: a text has fewer than 2^32 symbols.
 template <int VARIANT, int G>
-__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 ? 2 : (VARIANT >= 3 || G == 8 ? 3 : 4))
+__global__ void __launch_bounds__(kScanThreads, VARIANT == -2 || (G == 8 && VARIANT >= 3) ? 2 : (G == 8 ? 3 : 4))
     k_scan(const uint2 *__restrict__ planes, const PatDesc d, const uint4 *__restrict__ arena,
            TileEntry *__restrict__ table, pm_hit *__restrict__ tmp, uint64_t cap,
            unsigned long long *__restrict__ cursor, uint32_t *__restrict__ status,
@@ -191,14 +192,14 @@ const void *select_kernel(Variant v, int32_t k)
     case Variant::kWindowSliced:
         switch (k) {
         case 0: return kernel_ptr<0, 8>();
-        case 1: return kernel_ptr<1, 4>();
-        case 2: return kernel_ptr<2, 4>();
-        case 3: return kernel_ptr<3, 4>();
-        case 4: return kernel_ptr<4, 4>();
-        case 5: return kernel_ptr<5, 4>();
-        case 6: return kernel_ptr<6, 4>();
-        case 7: return kernel_ptr<7, 4>();
-        default: return kernel_ptr<8, 4>();
+        case 1: return kernel_ptr<1, 8>();
+        case 2: return kernel_ptr<2, 8>();
+        case 3: return kernel_ptr<3, 8>();
+        case 4: return kernel_ptr<4, 8>();
+        case 5: return kernel_ptr<5, 8>();
+        case 6: return kernel_ptr<6, 8>();
+        case 7: return kernel_ptr<7, 8>();
+        default: return kernel_ptr<8, 8>();
         }
     case Variant::kPatternSliced: return kernel_ptr<-1, 4>();
     case Variant::kPatternSliced2: return kernel_ptr<-3, 4>();

@@ -133,10 +133,15 @@ class Server:
     """Continuous-batching scheduler (see the module docstring)."""
 
     def __init__(self, backend, n: int, slots: int = 3, max_batch: int = 64,
-                 mem_budget: int = 8 << 30, clock=time.perf_counter, freqs: dict | None = None):
+                 mem_budget: int = 8 << 30, clock=time.perf_counter, freqs: dict | None = None,
+                 on_result=None, keep_hits: bool = True):
         """freqs: the text's letter frequencies for the admission model
         (default: the backend's ``letter_freqs()`` if it has one, else a
-        genome at 41 % GC)."""
+        genome at 41 % GC).  on_result: called with each completed Request
+        (hits attached) as soon as it completes.  keep_hits False: the server
+        lets go of a request's hits once on_result has seen them, so that their
+        memory (pinned host buffers) returns to the allocator; ``done`` then
+        keeps counts and times only."""
         self.backend = backend
         self.n = n
         if freqs is None and hasattr(backend, "letter_freqs"):
@@ -156,6 +161,8 @@ class Server:
         self._next = 0
         self.batches = 0
         self.max_inflight = 0
+        self.on_result = on_result
+        self.keep_hits = keep_hits
 
     def now(self) -> float:
         return self.clock() - self.t0
@@ -237,6 +244,10 @@ class Server:
                             self.cancelled.append(r)
                             continue
                         r.count, r.hits, r.done, r.status = c, h, t, "done"
+                        if self.on_result is not None:
+                            self.on_result(r)
+                        if not self.keep_hits:
+                            r.hits = None
                         self.done.append(r)
                         finished += 1
                 self.free_slots.append(f.slot)

@@ -198,3 +198,20 @@ def test_expected_hits_takes_the_text_letter_frequencies():
     srv = serve.Server(B(), n=n)
     r = srv.submit("SSSS", 0)   # S = C or G: never matches this text
     assert srv.freqs is f and r.capacity == serve.capacity_for("SSSS", 0, n, f) == 4096
+
+
+def test_results_go_to_the_consumer_and_can_be_released():
+    """on_result sees every completed query with its hits; with keep_hits
+    False the server keeps counts and times only."""
+    text = synth.markov_text(20_000, seed=61)
+    be = FakeBackend(text, delay=0.0)
+    seen = []
+    srv = serve.Server(be, n=text.size, slots=2, max_batch=4, mem_budget=1 << 40,
+                       on_result=lambda r: seen.append((r.qid, r.count, r.hits)), keep_hits=False)
+    for p, k in (("ACGTAC", 1), ("GGATCC", 0), ("TTRYAA", 2)):
+        srv.submit(p, k, arrival=0.0)
+    srv.drain()
+    assert sorted(q for q, _, _ in seen) == [0, 1, 2]
+    for qid, count, hits in seen:
+        assert hits is not None and len(hits[0]) == count
+    assert all(r.hits is None and r.count >= 0 for r in srv.done)

@@ -189,11 +189,12 @@ def test_noalloc_chunk_and_tile_limits():
     long_pat = pm.pm_compile_pattern("A" * (4096 * 32 + 1))  # 4097 chunks
     st, _ = _call_noalloc(L, small, [long_pat], [0], hits, offsets, 16)
     assert st == pm.PM_E_TOO_LARGE and b"chunks" in L.pm_last_error()
-    # 64 pairs at k = 1 (tiles of 4096 windows) over 140e6 symbols: 64 x 34180 > 2^21 tiles
+    # 64 pairs at k = 12 (pattern-sliced: tiles of 4096 windows) over 140e6
+    # symbols: 64 x 34180 > 2^21 tiles
     big = pm.pm_encode_text(synth.markov_text(140_000_000, seed=45))
-    p = pm.pm_compile_pattern("ACGTACGTAC")
-    st, _ = _call_noalloc(L, big, [p] * 64, [1] * 64, hits, offsets, 16)
+    p = pm.pm_compile_pattern("ACGTACGTAC" * 3 + "AC")
+    st, _ = _call_noalloc(L, big, [p] * 64, [12] * 64, hits, offsets, 16)
     assert st == pm.PM_E_TOO_LARGE and b"tiles" in L.pm_last_error()
     # the same search within the limit (fewer pairs) runs
-    st, needed = _call_noalloc(L, big, [p] * 8, [1] * 8, hits, offsets, 16)
+    st, needed = _call_noalloc(L, big, [p] * 8, [12] * 8, hits, offsets, 16)
     assert st in (pm.PM_OK, pm.PM_E_OVERFLOW) and needed > 0
