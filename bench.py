@@ -138,6 +138,7 @@ def args_():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: queries per second")
     ap.add_argument("--serve-mode", choices=("one-launch", "launch-per-query"), default="launch-per-query",
                     help="serving: one persistent launch per batch, or one scan launch per query")
+    ap.add_argument("--serve-slots", type=int, default=4, help="serving: batches in flight (streams)")
     ap.add_argument("--serve-delivery", choices=("host", "device"), default="host",
                     help="serving: hits delivered to pinned host memory (latency includes the copy) "
                          "or left on the device")
@@ -767,12 +768,13 @@ def run_serving(a):
     from paper_1611_06115_gb300 import tune
     tv = tune.tune_variants(text, kmax=max(q.k for q in qs) + 1)
     to_host = a.serve_delivery == "host"
-    backend = serve.GpuBackend(text, slots=4, batch={} if a.serve_mode == "one-launch" else None,
+    backend = serve.GpuBackend(text, slots=a.serve_slots, batch={} if a.serve_mode == "one-launch" else None,
                                copy_to_host=to_host)
     # the client takes each result as it completes and lets go of it, so the
     # pinned buffers return to the allocator
     def server():
-        return serve.Server(backend, n=n, slots=4, max_batch=32, mem_budget=32 << 30, keep_hits=False)
+        return serve.Server(backend, n=n, slots=a.serve_slots, max_batch=32, mem_budget=32 << 30,
+                            keep_hits=False)
     # warm the kernels, the device pool and the pinned-host pool
     serve.run_trace(server(), queries[:200])
     srv = server()
@@ -782,7 +784,8 @@ def run_serving(a):
     torch.cuda.synchronize()
     ck = clocks.stop()
     n_cells = sum((n - len(r.pattern) + 1) * len(r.pattern) for r in srv.done)
-    stats.update({"workload": "SERVING", "mode": a.serve_mode, "n": n, "offered_rate_qps": a.rate,
+    stats.update({"workload": "SERVING", "mode": a.serve_mode, "slots": a.serve_slots, "n": n,
+                  "offered_rate_qps": a.rate,
                   "variant_per_k": {str(k): VARIANT_NAMES[v] for k, v in enumerate(tv["table"])},
                   "arrival_seconds": a.duration, "queries": len(queries),
                   "window_cells_per_s": n_cells / stats["span_s"],

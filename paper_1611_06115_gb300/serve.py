@@ -329,12 +329,15 @@ class GpuBackend:
     launch per query, or with ``batch`` (batch options, {} for defaults) one
     persistent launch for the whole batch.
 
+    Each batch's offsets follow its search on the slot's stream into pinned
+    memory, so the host reads them without waiting on other work.
+
     copy_to_host: deliver each query's hits in pinned host memory.  Once a
-    batch's search has finished its offsets are read and one asynchronous
-    copy of the batch's hits into a pinned buffer is queued on the slot's
-    stream; the batch completes when that copy has landed, so latency
-    includes the copy to the caller.  Otherwise the hits stay on the device
-    and a batch completes with its search."""
+    batch's search has finished, one asynchronous copy of the batch's hits
+    into a pinned buffer is queued on the slot's stream; the batch completes
+    when that copy has landed, so latency includes the copy to the caller.
+    Otherwise the hits stay on the device and a batch completes with its
+    search."""
 
     def __init__(self, text, slots: int = 3, copy_to_host: bool = False, batch: dict | None = None):
         import torch
@@ -373,10 +376,14 @@ class GpuBackend:
             res = self.api.pm_search_ex(self.text, [self._pattern(r.pattern) for r in reqs],
                                         [r.k for r in reqs], capacity=cap, stream=st, sync=False,
                                         batch=self.batch)
+            # the offsets follow the search on its stream into pinned memory, so
+            # reading them later waits for nothing else on the device
+            off = torch.empty(res.offsets.shape, dtype=res.offsets.dtype, pin_memory=True)
+            off.copy_(res.offsets, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        # [result, search event, capacity, slot, offsets (host), host hits, copy event]
-        return [res, ev, cap, slot, None, None, None]
+        # [result, search event, capacity, slot, offsets (pinned host), host hits, copy event]
+        return [res, ev, cap, slot, off, None, None]
 
     def ready(self, handle) -> bool:
         res, ev, cap, slot = handle[0], handle[1], handle[2], handle[3]
@@ -385,7 +392,7 @@ class GpuBackend:
         if handle[6] is None:
             if not ev.query():
                 return False
-            off = res.offsets.cpu().numpy().astype(np.uint64)  # search done: a short copy
+            off = handle[4].numpy().astype(np.uint64)  # landed with the search
             handle[4] = off
             total = int(off[-1])
             if total > cap or total == 0:
@@ -403,7 +410,9 @@ class GpuBackend:
 
     def collect(self, handle, reqs):
         res, cap = handle[0], handle[2]
-        off = handle[4] if handle[4] is not None else res.offsets.cpu().numpy().astype(np.uint64)
+        off = handle[4]
+        if not isinstance(off, np.ndarray):
+            off = off.numpy().astype(np.uint64)  # landed with the search
         total = int(off[-1])
         counts = [int(off[i + 1] - off[i]) for i in range(len(reqs))]
         if total > cap:
