@@ -44,6 +44,10 @@ namespace pm {
 namespace {
 constexpr int kP = 8;  // pairs per group
 constexpr uint32_t kSpassWords = kP * scan::G * 32;  // pass words of one pattern-sliced row and tile
+// 32-window groups per lane in a warp tile of category cat: eight for the
+// window-sliced launches (the per-tile work spread over 8192 windows, as in
+// the per-pattern kernels), four for the others
+constexpr int cat_groups(int cat) { return cat <= kWsMaxK ? 8 : scan::G; }
 // group kinds
 constexpr uint32_t kKindShort = 0;   // pattern-sliced over positions 0..31, shared shifts (k <= 31)
 constexpr uint32_t kKindWs = 1;      // window-sliced (k <= kWsMaxK)
@@ -71,8 +75,10 @@ struct pm_batch {
     int grid;          // CTAs per launch (0: as many as each category's kernel keeps resident)
     int key_bits;
     uint32_t tiles;    // warp tiles per work item
-    uint64_t ntiles;   // warp tiles of the longest window range
-    uint64_t runs;     // runs of `tiles` tiles covering them
+    uint64_t ntiles;   // 4096-window tiles of the longest window range
+    uint64_t runs;     // runs of `tiles` such tiles covering them
+    uint64_t maxwin;   // that window range (windows of the shortest pattern)
+    uint64_t key_stride;  // record keys per pair (record_key)
     uint64_t capacity;
     const uint2 *planes;  // the text's planes (not owned)
     const uint32_t *unk;  // the text's unknown-symbol bits or NULL (not owned)
@@ -106,7 +112,8 @@ struct BatchArgs {
     const uint4 *arena;
     uint32_t npat, ngroups;
     uint32_t tiles;         // warp tiles per item
-    uint64_t ntiles, runs;  // items = rows * runs, row-major
+    uint64_t ntiles, runs;  // this launch's tiles; items = rows * runs, run-major
+    uint64_t key_stride;    // record keys of pair p: p * key_stride + its group index
     uint64_t items;
     pm_hit *tmp;
     uint64_t cap;
@@ -117,6 +124,15 @@ struct BatchArgs {
     unsigned long long *pat_counts;
     uint32_t *status;
 };
+
+// The sort key of the record of pair p that starts at group `group` of the
+// text (tile * groups per tile + group within the tile): pairs in order,
+// then the text's groups in order, whatever the tile width of the pair's
+// category.
+__device__ __forceinline__ unsigned long long record_key(const BatchArgs &ba, uint32_t p, uint64_t group)
+{
+    return (unsigned long long)p * ba.key_stride + group;
+}
 
 // Append one segment record: `count` hits of pair p at tmp[base ..], in
 // window order, for the (pair, tile, group) of `key`.  One lane calls it.
@@ -186,36 +202,53 @@ __device__ __forceinline__ uint32_t pair_valid(const RowPair &r, uint64_t tile, 
 }
 
 // The candidates of pair rp in NG groups (g0 .. g0+NG-1) of one staged warp
-// tile, settled by the whole warp from its shared-memory queue q as in
-// settle_emit_queued (see pm_scan_impl.cuh), the hits written once and
-// described by one segment record whose key is that of group g0.  Returns
-// false, having done nothing, when there are more than kQueueCap candidates
-// or k >= 2^20.  Call with the whole warp.
-template <int NG>
+// tile of GB groups per lane, settled by the whole warp from its
+// shared-memory queue q as in settle_emit_queued (see pm_scan_impl.cuh),
+// the hits written once and described by one segment record whose key is
+// that of group g0.  Returns false, having done nothing, when there are more
+// than kQueueCap candidates or k is too large for a count to share 32 bits
+// with its window.  Call with the whole warp.
+template <int NG, int GB>
 __device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], uint32_t g0, uint64_t tile,
                                                    const uint2 *stage, uint32_t *q, const RowPair &rp,
                                                    const BatchArgs &ba)
 {
-    static_assert(NG == 1 || NG == 4, "one group or a whole tile");
+    static_assert(NG == 1 || NG == 4 || NG == 8, "one group or four or eight");
+    static_assert((GB == 4 || GB == 8) && NG <= GB, "tiles of four or eight groups");
+    constexpr int NW = (NG + 3) / 4;                     // words of packed group counts
+    constexpr uint32_t kWinBits = GB == 4 ? 12u : 13u;  // window within the tile
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t k = rp.k;
     const uint4 *__restrict__ M = ba.arena + rp.masks;
-    uint32_t packed = 0;
+    // byte j of word i: this lane's candidates in group g0 + 4i + j
+    uint32_t packed[NW];
+    uint32_t mine = 0;
 #pragma unroll
-    for (int i = 0; i < NG; ++i) packed |= (uint32_t)__popc(cand[i]) << (8 * i);
-    const uint32_t total = __reduce_add_sync(kFull, (packed * 0x01010101u) >> 24);
-    if (total > kQueueCap || k >= (1u << 20)) return false;
-    uint32_t incl = packed;
+    for (int i = 0; i < NW; ++i) {
+        packed[i] = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (uint32_t)o) incl += v;
+        for (int j = 0; j < 4 && 4 * i + j < NG; ++j) packed[i] |= (uint32_t)__popc(cand[4 * i + j]) << (8 * j);
+        mine += (packed[i] * 0x01010101u) >> 24;
     }
-    const uint32_t tot = __shfl_sync(kFull, incl, 31);
-    const uint32_t pos = tot * 0x01010100u + (incl - packed);  // bytes never carry: total <= 255
+    const uint32_t total = __reduce_add_sync(kFull, mine);
+    if (total > kQueueCap || k >= (1u << (32u - kWinBits))) return false;
+    uint32_t pos[NW];
+    uint32_t before = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        uint32_t incl = packed[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (uint32_t)o) incl += v;
+        }
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        pos[i] = before * 0x01010101u + tot * 0x01010100u + (incl - packed[i]);  // bytes never carry
+        before += (tot * 0x01010101u) >> 24;
+    }
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
-        uint32_t at = (pos >> (8 * i)) & 0xffu;
+        uint32_t at = (pos[i / 4] >> (8 * (i % 4))) & 0xffu;
         uint32_t m = cand[i];
         while (m) {
             const uint32_t w = __ffs(m) - 1;
@@ -232,10 +265,10 @@ __device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], u
         if (i < total) {
             const uint32_t e = q[i];
             const uint32_t gl = e >> 5;  // block within the tile
-            const uint32_t c = candidate_count(stage + gl, tile * (32ull * G) + gl, e & 31u, M, 0u, rp.nchunks, k,
-                                               ba.planes, ba.unk);
+            const uint32_t c = candidate_count(stage + gl, tile * (32ull * GB) + gl, e & 31u, M, 0u, rp.nchunks,
+                                               k, ba.planes, ba.unk);
             hit = c <= k;
-            rec = e | (c << 12);
+            rec = e | (c << kWinBits);
         }
         const uint32_t hb = __ballot_sync(kFull, hit);
         __syncwarp();  // every entry of this round is read before any is overwritten
@@ -247,13 +280,14 @@ __device__ __forceinline__ bool settle_emit_record(const uint32_t (&cand)[NG], u
         unsigned long long base = 0;
         if (lane == 0) {
             base = atomicAdd(ba.cursor, (unsigned long long)hits);
-            put_record(ba, rp.p, ((unsigned long long)rp.p * ba.ntiles + tile) * G + g0, base, hits);
+            put_record(ba, rp.p, record_key(ba, rp.p, tile * GB + g0), base, hits);
         }
         base = __shfl_sync(kFull, base, 0);
-        const uint64_t w0 = tile * kTileWindows;
+        const uint64_t w0 = tile * (1024ull * GB);
         for (uint32_t i = lane; i < hits; i += 32) {
             const uint32_t r = q[i];
-            if (base + i < ba.cap) ba.tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & 4095u)), r >> 12};
+            if (base + i < ba.cap)
+                ba.tmp[base + i] = pm_hit{(uint32_t)(w0 + (r & ((1u << kWinBits) - 1u))), r >> kWinBits};
         }
     }
     __syncwarp();  // the queue is rewritten next
@@ -344,7 +378,7 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
             pass[g] = spass[(p * G + g) * 32 + lane] & pair_valid(r, tile, blk[g]);
             anyr |= pass[g];
         }
-        if (!__any_sync(kFull, anyr != 0u) || settle_emit_record<G>(pass, 0u, tile, stage, q, r, ba)) continue;
+        if (!__any_sync(kFull, anyr != 0u) || settle_emit_record<G, G>(pass, 0u, tile, stage, q, r, ba)) continue;
         const uint4 *M = ba.arena + r.masks;
 #pragma unroll 1
         for (int g = 0; g < G; ++g) {
@@ -355,44 +389,44 @@ __device__ __forceinline__ void short_group(const uint2 *stage, uint64_t tile, u
                 ps = settle_staged(ps, blk[0] + 32ull * g, stage[32 * g + lane], stage[32 * g + lane + 1],
                                    stage + 32 * g + lane + 2, M, 0u, r.nchunks, r.k, ba.planes);
             if (__any_sync(kFull, ps != 0u))
-                emit_group(ps, blk[0] + 32ull * g, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
+                emit_group(ps, blk[0] + 32ull * g, r.p, record_key(ba, r.p, tile * G + g),
                            r.nchunks, r.k, M, ba);
         }
     }
     __syncwarp();  // spass is rewritten by the next tile
 }
 
-// Window-sliced pair rp over one staged tile (a, b: the lane's blocks; list:
-// the pair's compact list in shared memory): the thermometer scan of
-// alive_window_sliced over the tile's four groups at once, the candidates
+// Window-sliced pair rp over one staged tile of GB groups per lane (a, b:
+// the lane's blocks; list: the pair's compact list in shared memory): the
+// scan of alive_window_sliced over all groups at once, the candidates
 // settled by the warp together.
-template <int K>
-__device__ __forceinline__ void ws_pair(const uint2 (&a)[G], const uint2 (&b)[G], const uint2 *stage,
+template <int K, int GB>
+__device__ __forceinline__ void ws_pair(const uint2 (&a)[GB], const uint2 (&b)[GB], const uint2 *stage,
                                         uint64_t tile, const RowPair &rp, const uint32_t *list, uint32_t *q,
                                         const BatchArgs &ba)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t valid[G], pass[G];
-    uint64_t blk[G];
+    uint32_t valid[GB], pass[GB];
+    uint64_t blk[GB];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        blk[g] = tile * (32ull * G) + 32ull * g + (uint64_t)lane;
+    for (int g = 0; g < GB; ++g) {
+        blk[g] = tile * (32ull * GB) + 32ull * g + (uint64_t)lane;
         valid[g] = pair_valid(rp, tile, blk[g]);
     }
     const bool cut =
         alive_window_sliced<K>(a, b, list, rp.lists & 0xffu, rp.lists >> 8, ws_cut(K), valid, pass);
     uint32_t anyp = 0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) anyp |= pass[g];
-    if (__any_sync(kFull, anyp != 0u) && !settle_emit_record<G>(pass, 0u, tile, stage, q, rp, ba)) {
+    for (int g = 0; g < GB; ++g) anyp |= pass[g];
+    if (__any_sync(kFull, anyp != 0u) && !settle_emit_record<GB, GB>(pass, 0u, tile, stage, q, rp, ba)) {
         const uint4 *M = ba.arena + rp.masks;
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
+        for (int g = 0; g < GB; ++g) {
             const uint32_t ps = (cut || rp.nchunks > 1)
                                     ? settle_from_regs(pass[g], blk[g], a[g], b[g], M, rp.nchunks, rp.k, ba.planes)
                                     : pass[g];
             if (__any_sync(kFull, ps != 0u))
-                emit_group(ps, blk[g], rp.p, ((unsigned long long)rp.p * ba.ntiles + tile) * G + g, rp.nchunks,
+                emit_group(ps, blk[g], rp.p, record_key(ba, rp.p, tile * GB + g), rp.nchunks,
                            rp.k, M, ba);
         }
     }
@@ -412,20 +446,29 @@ __device__ __forceinline__ void ws_pair(const uint2 (&a)[G], const uint2 (&b)[G]
 // the tiles of its whole sequence of items are staged kStages ahead by the
 // lanes' own asynchronous copies, and a stage is refilled once the warp is
 // done with its tile.
+//
+// Window-sliced launches run tiles of eight groups per lane (8192 windows),
+// two CTAs per SM (measured faster than three, whose 80 registers spill at
+// k <= 2), the others tiles of four (cat_groups); the stages (and a
+// pattern-sliced row's pass words) sit in dynamic shared memory
+// (batched_smem).
 template <int CAT>
-__global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArgs ba)
+__global__ void __launch_bounds__(kScanThreads, CAT <= kWsMaxK ? 2 : 3)
+    k_scan_batched(const BatchArgs ba)
 {
     constexpr bool kWsCat = CAT <= kWsMaxK;
+    constexpr int GB = cat_groups(CAT);
     constexpr uint32_t S = kStages;
-    constexpr uint32_t kSB = scan_stage_blocks<G>();
-    __shared__ __align__(128) uint2 sbuf[kScanWarps][S][kSB];
+    constexpr uint32_t kSB = scan_stage_blocks<GB>();
+    extern __shared__ __align__(128) uint2 dsmem[];
+    uint2 (*sbuf)[S][kSB] = reinterpret_cast<uint2 (*)[S][kSB]>(dsmem);  // [kScanWarps][S][kSB]
+    uint32_t *spass = reinterpret_cast<uint32_t *>(dsmem + kScanWarps * S * kSB);  // kSpassWords per warp
     __shared__ uint32_t squeue[kScanWarps][kQueueCap];
     __shared__ RowPair srow[kScanWarps][kP];
     __shared__ uint32_t slist[kScanWarps][kWsCat ? kP : 1][32];
     __shared__ uint4 sM0[kScanWarps][kP];
     __shared__ uint4 sM1[kScanWarps][kP];
     __shared__ uint4 sP[kScanWarps][kP];  // pattern-sliced group: {k in every byte, 0, 0, 0}
-    extern __shared__ uint32_t spass[];  // pattern-sliced row: its pass words, kSpassWords per warp
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -443,7 +486,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
     for (uint32_t st = 0; st < S; ++st) {
         if (pi < items) {
             const uint64_t t = tile_of(pi, pu);
-            if (t < ntiles) copy_tile_async<G>(ba.planes, t * (32u * G), &sbuf[warp][st][0], lane);
+            if (t < ntiles) copy_tile_async<GB>(ba.planes, t * (32u * GB), &sbuf[warp][st][0], lane);
         }
         cp_async_commit();
         if (++pu == T) {
@@ -477,7 +520,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
             r.masks = (uint32_t)d.masks;
             r.lists = d.n_single | (d.n_general << 8);
             r.ntiles = (uint32_t)d.ntiles;
-            r.nfull = (uint32_t)(d.nwin / kTileWindows);
+            r.nfull = (uint32_t)(d.nwin / (1024u * GB));
             r.pad = 0;
             r.nwin = d.nwin;
             srow[warp][lane] = r;
@@ -512,16 +555,16 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
             const uint2 *stage = &sbuf[warp][st][0];
             if (tile < ntiles) {
                 if constexpr (kWsCat) {
-                    uint2 a[G], b[G];
+                    uint2 a[GB], b[GB];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
+                    for (int g = 0; g < GB; ++g) {
                         a[g] = stage[32 * g + lane];
                         b[g] = stage[32 * g + lane + 1];
                     }
                     for (uint32_t i = 0; i < cnt; ++i) {
                         const RowPair &r = srow[warp][i];
                         if (tile >= r.ntiles) continue;  // this pair's windows end before the tile
-                        ws_pair<CAT>(a, b, stage, tile, r, slist[warp][i], squeue[warp], ba);
+                        ws_pair<CAT, GB>(a, b, stage, tile, r, slist[warp][i], squeue[warp], ba);
                     }
                 } else if constexpr (CAT == kCatLong) {
                     for (uint32_t i = 0; i < cnt; ++i) {
@@ -535,8 +578,8 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
                                                                  pair_valid(r, tile, blk), stage[32 * g + lane],
                                                                  stage[32 * g + lane + 1])};
                             if (__any_sync(kFull, pass[0] != 0u) &&
-                                !settle_emit_record<1>(pass, (uint32_t)g, tile, stage, squeue[warp], r, ba))
-                                emit_group(pass[0], blk, r.p, ((unsigned long long)r.p * ba.ntiles + tile) * G + g,
+                                !settle_emit_record<1, G>(pass, (uint32_t)g, tile, stage, squeue[warp], r, ba))
+                                emit_group(pass[0], blk, r.p, record_key(ba, r.p, tile * G + g),
                                            r.nchunks, r.k, M, ba);
                         }
                     }
@@ -550,7 +593,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_batched(const BatchArg
             __syncwarp();
             if (pi < items) {
                 const uint64_t t = tile_of(pi, pu);
-                if (t < ntiles) copy_tile_async<G>(ba.planes, t * (32u * G), &sbuf[warp][st][0], lane);
+                if (t < ntiles) copy_tile_async<GB>(ba.planes, t * (32u * GB), &sbuf[warp][st][0], lane);
             }
             cp_async_commit();
             if (++pu == T) {
@@ -590,12 +633,13 @@ const void *batched_kernel(int cat)
 }
 static_assert(kWsMaxK == 8, "one window-sliced launch per k = 0 .. 8");
 
-// Dynamic shared memory of a launch of category cat: the pass words of a
-// pattern-sliced row (with the static arrays past the 48 KB that static
-// shared memory may hold).
+// Dynamic shared memory of a launch of category cat: the stages of its
+// warps and, for a pattern-sliced row, its pass words (with the static
+// arrays past the 48 KB that static shared memory may hold).
 size_t batched_smem(int cat)
 {
-    return cat == kCatPs1 || cat == kCatPs2 ? (size_t)kScanWarps * kSpassWords * sizeof(uint32_t) : 0;
+    const size_t stages = (size_t)kScanWarps * kStages * (32u * cat_groups(cat) + 4u) * sizeof(uint2);
+    return stages + (cat == kCatPs1 || cat == kCatPs2 ? (size_t)kScanWarps * kSpassWords * sizeof(uint32_t) : 0);
 }
 
 // Sets the kernel of category cat up on the current device (its dynamic
@@ -635,7 +679,9 @@ struct BatchPlan {
     uint32_t cat_rows[kCats][2] = {};
     int grid = 0;
     uint32_t tiles = 1;
-    uint64_t ntiles = 0, runs = 0;
+    uint64_t ntiles = 0, runs = 0;  // in 4096-window tiles
+    uint64_t maxwin = 0;            // windows of the shortest pattern
+    uint64_t key_stride = 0;        // record keys per pair
     int key_bits = 0;
 };
 
@@ -740,6 +786,8 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
                          : v == Variant::kPatternSliced2 ? kCatPs2
                                                          : kCatLong;
         cats[c].push_back(p);
+        const uint64_t tw = 1024ull * (uint64_t)cat_groups((int)c);  // the category's tile
+        desc[p].ntiles = (desc[p].nwin + tw - 1) / tw;
     }
     // gkind: bits 0-1 the kind, bits 2.. the number of real pairs (the last
     // group of a category is padded to kP slots with repeats of its first
@@ -765,13 +813,18 @@ pm_status plan_batch(const char *who, const pm_text *text, const pm_pattern *con
         pl.cat_rows[c][1] = (uint32_t)pl.phases.size();
     }
     pl.grid = o.grid > 0 ? o.grid : 0;
-    pl.ntiles = min_m <= text->n ? (text->n - min_m + 1 + kTileWindows - 1) / kTileWindows : 0;
+    pl.maxwin = min_m <= text->n ? text->n - min_m + 1 : 0;
+    pl.ntiles = (pl.maxwin + kTileWindows - 1) / kTileWindows;  // in the smallest tiles
     // item numbers (runs * rows of a category) stay below 2^31
     const uint64_t rows = std::max<uint64_t>(pl.phases.size(), 1);
     while ((pl.ntiles + tiles - 1) / tiles * rows >= (1ull << 31)) tiles *= 2;
     pl.tiles = tiles;
     pl.runs = (pl.ntiles + tiles - 1) / tiles;
-    const unsigned long long max_key = (unsigned long long)npat * (pl.ntiles ? pl.ntiles : 1) * G;
+    // keys: pair * key_stride + group of the text (record_key); the stride
+    // covers the groups of both tile widths
+    pl.key_stride = std::max<uint64_t>(std::max<uint64_t>(pl.ntiles, 1) * (uint64_t)G,
+                                       ((pl.maxwin + 8191) / 8192) * 8ull);
+    const unsigned long long max_key = (unsigned long long)npat * pl.key_stride;
     pl.key_bits = 0;
     while (pl.key_bits < 64 && (max_key >> pl.key_bits) != 0) ++pl.key_bits;
     return PM_OK;
@@ -827,6 +880,8 @@ void fill_batch(const BatchPlan &pl, const pm_text *text, uint32_t npat, uint64_
     b->ntiles = pl.ntiles;
     b->tiles = pl.tiles;
     b->runs = pl.runs;
+    b->maxwin = pl.maxwin;
+    b->key_stride = pl.key_stride;
     b->nphases = (uint32_t)pl.phases.size();
     b->capacity = capacity;
     b->planes = text->planes;
@@ -868,10 +923,13 @@ pm_status run_batch(const pm_batch *b, pm_hit *hits, uint64_t *offsets, cudaStre
     // one persistent launch per category present, back to back on the stream
     for (int cat = 0; !rc && cat < kCats; ++cat) {
         const uint32_t r0 = b->cat_rows[cat][0], r1 = b->cat_rows[cat][1];
-        const uint64_t items = b->runs * (uint64_t)(r1 - r0);
+        // the category's tiles (eight or four groups per lane) and runs of them
+        const uint64_t tw = 1024ull * (uint64_t)cat_groups(cat);
+        const uint64_t ntiles = (b->maxwin + tw - 1) / tw, runs = (ntiles + b->tiles - 1) / b->tiles;
+        const uint64_t items = runs * (uint64_t)(r1 - r0);
         if (items == 0) continue;
         BatchArgs ba{b->planes, b->unk, b->pats,  b->order,  b->gkind, b->phases + r0, b->arena,
-                     b->npat,   b->ngroups, b->tiles, b->ntiles, b->runs, items,
+                     b->npat,   b->ngroups, b->tiles, ntiles, runs, b->key_stride, items,
                      b->tmp,    b->capacity, cursor,  b->recs,  b->capacity, rec_cursor,
                      b->pat_counts, status};
         uint64_t grid = (items + kScanWarps - 1) / kScanWarps;
