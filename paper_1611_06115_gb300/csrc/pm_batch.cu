@@ -448,12 +448,13 @@ __device__ __forceinline__ void ws_pair(const uint2 (&a)[GB], const uint2 (&b)[G
 // done with its tile.
 //
 // Window-sliced launches run tiles of eight groups per lane (8192 windows),
-// two CTAs per SM (measured faster than three, whose 80 registers spill at
-// k <= 2), the others tiles of four (cat_groups); the stages (and a
+// the others tiles of four (cat_groups).  The window-sliced and every-chunk
+// launches run two CTAs per SM (measured faster than three, whose 80
+// registers spill), the pattern-sliced ones three.  The stages (and a
 // pattern-sliced row's pass words) sit in dynamic shared memory
 // (batched_smem).
 template <int CAT>
-__global__ void __launch_bounds__(kScanThreads, CAT <= kWsMaxK ? 2 : 3)
+__global__ void __launch_bounds__(kScanThreads, CAT <= kWsMaxK || CAT == kCatLong ? 2 : 3)
     k_scan_batched(const BatchArgs ba)
 {
     constexpr bool kWsCat = CAT <= kWsMaxK;
