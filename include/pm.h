@@ -294,18 +294,18 @@ pm_status pm_get_auto_variants(int32_t *out, uint32_t nk);
  *                  pattern handles may be freed afterwards; the text must
  *                  outlive the batch.  Waits for its uploads.
  * options          NULL for defaults, or (0 in any field: its default):
- *                    group      pairs per work item row, rounded up to a
- *                               multiple of 8 (default: every pair of the
- *                               row's kind);
- *                    grid       CTAs of the persistent launch (default: as
+ *                    group      accepted for compatibility and not used
+ *                               (a work item row is one group of 8 pairs);
+ *                    grid       CTAs of each persistent launch (default: as
  *                               many as the device keeps resident);
- *                    tiles      warp tiles of 4096 windows per work item,
- *                               1..4 (default 1);
+ *                    tiles      warp tiles per work item, 1..64 (default 16;
+ *                               a tile is 8192 windows for window-sliced
+ *                               pairs, 4096 for the others);
  *                    ws_below   pairs with k < ws_below are evaluated
  *                               window-sliced, 1..9 (default 9; -1: none);
  *                    ps1_below  other pairs with k < ps1_below are evaluated
- *                               pattern-sliced over positions 0..31, then
- *                               settled one window at a time, 1..32
+ *                               pattern-sliced over positions 0..31, their
+ *                               survivors then counted exactly, 1..32
  *                               (default 18; -1: none);
  *                    ps2_below  other pairs with k < ps2_below over
  *                               positions 0..63, 1..64 (default 41; -1:
@@ -363,8 +363,9 @@ void pm_batch_free(pm_batch *batch);
  * Limits (PM_E_TOO_LARGE beyond them, nothing queued): at most 64 (pattern,
  * k) pairs, at most 4096 32-position chunks over the distinct patterns
  * (e.g. m up to 131072 for one pattern), at most 2^21 warp tiles over all
- * pairs (a tile is 4096 windows, 8192 for a window-sliced pair with k = 0;
- * e.g. 8.6e9 windows for one pattern), capacity at most 2^22 hits.
+ * pairs (a tile is 8192 windows for a window-sliced pair, k <= 8, else
+ * 4096; e.g. 8.6e9 windows for one pattern with k > 8), capacity at most
+ * 2^22 hits.
  *
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
