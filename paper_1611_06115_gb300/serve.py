@@ -139,9 +139,10 @@ class Server:
         (default: the backend's ``letter_freqs()`` if it has one, else a
         genome at 41 % GC).  on_result: called with each completed Request
         (hits attached) as soon as it completes.  keep_hits False: the server
-        lets go of a request's hits once on_result has seen them, so that their
-        memory (pinned host buffers) returns to the allocator; ``done`` then
-        keeps counts and times only."""
+        lets go of a request's hits once on_result has seen them and hands the
+        batch's buffers back to the backend for reuse (``release``), so the
+        hits are valid during on_result only (copy what must outlive it);
+        ``done`` then keeps counts and times only."""
         self.backend = backend
         self.n = n
         if freqs is None and hasattr(backend, "letter_freqs"):
@@ -238,6 +239,8 @@ class Server:
                         r.capacity, r.retries = max(r.capacity, c), r.retries + 1
                         r.status = "queued"
                         self.queue.appendleft(r)
+                    if hasattr(self.backend, "release"):
+                        self.backend.release(f.handle)  # nothing was handed out
                 else:
                     for r, c, h in zip(f.reqs, counts, hits):
                         if r.status == "cancelled":
@@ -250,6 +253,8 @@ class Server:
                             r.hits = None
                         self.done.append(r)
                         finished += 1
+                    if not self.keep_hits and hasattr(self.backend, "release"):
+                        self.backend.release(f.handle)
                 self.free_slots.append(f.slot)
                 self.inflight_bytes -= f.nbytes
             else:
@@ -349,6 +354,7 @@ class GpuBackend:
         self.copy_to_host = copy_to_host
         self.batch = batch
         self._compiled: dict[str, object] = {}
+        self._free: dict[int, list] = {}  # pinned buffers by size (bytes), for reuse
 
     def letter_freqs(self) -> dict:
         """The resident text's letter frequencies (measured when it was coded)."""
@@ -360,6 +366,27 @@ class GpuBackend:
             c = self.api.pm_compile_pattern(p)
             self._compiled[p] = c
         return c
+
+    def _pinned(self, nbytes: int):
+        """A page-locked host buffer (uint8) of at least nbytes: a released one
+        of the same power-of-two size when there is one, else a new one
+        (pinning pages takes the host thread milliseconds per large buffer)."""
+        size = 1 << 16
+        while size < nbytes:
+            size <<= 1
+        free = self._free.get(size)
+        if free:
+            return free.pop()
+        return self.torch.empty(size, dtype=self.torch.uint8, pin_memory=True)
+
+    def release(self, handle) -> None:
+        """Take back a finished batch's pinned buffers for later batches.  The
+        server calls this once the batch's results were delivered and nobody
+        holds them any more (Server keep_hits=False), or when the batch's
+        output did not fit (nothing was handed out)."""
+        for buf in handle[7]:
+            self._free.setdefault(buf.numel(), []).append(buf)
+        handle[7] = []
 
     def bytes_for(self, reqs, n: int) -> int:
         cap = sum(r.capacity for r in reqs)
@@ -378,12 +405,15 @@ class GpuBackend:
                                         batch=self.batch)
             # the offsets follow the search on its stream into pinned memory, so
             # reading them later waits for nothing else on the device
-            off = torch.empty(res.offsets.shape, dtype=res.offsets.dtype, pin_memory=True)
+            nb = res.offsets.numel() * res.offsets.element_size()
+            obuf = self._pinned(nb)
+            off = obuf[:nb].view(res.offsets.dtype)
             off.copy_(res.offsets, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        # [result, search event, capacity, slot, offsets (pinned host), host hits, copy event]
-        return [res, ev, cap, slot, off, None, None]
+        # [result, search event, capacity, slot, offsets (pinned host), host hits,
+        #  copy event, pinned buffers of the batch]
+        return [res, ev, cap, slot, off, None, None, [obuf]]
 
     def ready(self, handle) -> bool:
         res, ev, cap, slot = handle[0], handle[1], handle[2], handle[3]
@@ -399,7 +429,9 @@ class GpuBackend:
                 return True
             torch = self.torch
             st = self.streams[slot]
-            host = torch.empty((total, 2), dtype=torch.int32, pin_memory=True)
+            hbuf = self._pinned(8 * total)
+            handle[7].append(hbuf)
+            host = hbuf[:8 * total].view(torch.int32).view(total, 2)
             with torch.cuda.stream(st):
                 host.copy_(res.hits[:total], non_blocking=True)
                 cev = torch.cuda.Event()

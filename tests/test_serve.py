@@ -215,3 +215,27 @@ def test_results_go_to_the_consumer_and_can_be_released():
     for qid, count, hits in seen:
         assert hits is not None and len(hits[0]) == count
     assert all(r.hits is None and r.count >= 0 for r in srv.done)
+
+
+def test_released_batches_go_back_to_the_backend():
+    """With keep_hits False every finished batch is handed back (release)
+    after its results were delivered; with keep_hits True only batches whose
+    output did not fit are."""
+    text = synth.markov_text(20_000, seed=62)
+
+    class Releasing(FakeBackend):
+        def __init__(self, *a, **k):
+            super().__init__(*a, **k)
+            self.released = []
+
+        def release(self, h):
+            self.released.append(h)
+
+    for keep in (False, True):
+        be = Releasing(text, delay=0.0)
+        srv = serve.Server(be, n=text.size, slots=2, max_batch=2, mem_budget=1 << 40, keep_hits=keep)
+        for p, k in (("ACGTAC", 1), ("GGATCC", 0), ("TTRYAA", 2), ("ACGTNN", 1)):
+            srv.submit(p, k, arrival=0.0)
+        srv.drain()
+        assert len(srv.done) == 4
+        assert len(be.released) == (len(be.launched) if not keep else 0)
