@@ -80,7 +80,7 @@ def traffic(kernel, n):
 
 
 # First-stage ALU-pipe instructions per window of each evaluation (the
-# roofline's algorithmic work; the design doc section 7 derives them):
+# roofline's algorithmic work, counted from the evaluations' definitions):
 #   pattern-sliced over 32 positions: 2 funnel shifts + 3 selects = 5;
 #   over 64 positions: 10;
 #   window-sliced: per listed position and 32 windows one funnel shift plus
