@@ -288,9 +288,11 @@ class Server:
 
 def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
     """Replay a list of (arrival seconds, pattern, k) on the server's clock in
-    real time, then drain.  Returns throughput, latency percentiles and the
-    queue depth (queries waiting for a slot), time-weighted over the arrival
-    period and at its peak."""
+    real time, then drain.  Returns throughput (all queries over the whole
+    span, start-up and drain included; and the steady-state completion rate
+    over the last nine tenths of the arrival period), latency percentiles and
+    the queue depth (queries waiting for a slot), time-weighted over the
+    arrival period and at its peak."""
     queries = sorted(queries, key=lambda q: q[0])
     i = 0
     t_start = server.now()
@@ -311,10 +313,16 @@ def run_trace(server: Server, queries, poll: float = 0.0002) -> dict:
     t_end = server.now()
     lat = np.array([r.latency for r in server.done])
     span = t_end - t_start
+    # completion rate in steady state: queries completed between the end of
+    # the first tenth of the arrival period and its end, per second of that
+    # interval (no start-up, no drain)
+    w0, w1 = t_start + 0.1 * t_arrivals_end, t_start + t_arrivals_end
+    in_window = sum(1 for r in server.done if r.done is not None and w0 <= r.done < w1)
     return {
         "completed": len(server.done),
         "offered_qps": len(queries) / max(queries[-1][0], 1e-9) if queries else 0.0,
         "throughput_qps": len(server.done) / span if span > 0 else 0.0,
+        "steady_qps": in_window / (w1 - w0) if w1 > w0 else 0.0,
         "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
         "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
         "span_s": span,

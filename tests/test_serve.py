@@ -239,3 +239,16 @@ def test_released_batches_go_back_to_the_backend():
         srv.drain()
         assert len(srv.done) == 4
         assert len(be.released) == (len(be.launched) if not keep else 0)
+
+
+def test_steady_rate_counts_completions_inside_the_arrival_period():
+    """steady_qps: completions between 10 % and 100 % of the arrival period
+    per second of that interval; a server that keeps up reports about the
+    offered rate there."""
+    text = synth.markov_text(50_000, seed=63)
+    be = FakeBackend(text, delay=0.001)
+    srv = serve.Server(be, n=text.size, slots=4, max_batch=2, mem_budget=1 << 40)
+    queries = [(0.005 * i, "ACGTAC", 1) for i in range(60)]  # 200 q/s for 0.3 s
+    st = serve.run_trace(srv, queries)
+    assert st["completed"] == 60
+    assert 150 <= st["steady_qps"] <= 250, st["steady_qps"]
