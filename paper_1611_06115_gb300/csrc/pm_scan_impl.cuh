@@ -545,25 +545,31 @@ __device__ __forceinline__ uint32_t pass_multi_chunk(const uint2 *__restrict__ p
                                                      const uint4 *__restrict__ M, uint32_t nchunks,
                                                      uint32_t k, uint32_t valid, uint2 t0, uint2 t1)
 {
+    // counts only grow, so a window is a hit iff its final count is at most
+    // k; the loop only needs the lane's smallest count to know whether any
+    // of its windows is still at or below k (invalid windows start far past
+    // any k, so they never keep it going)
+    constexpr uint32_t kPast = 1u << 30;
     uint32_t cnt[32];
 #pragma unroll
-    for (int w = 0; w < 32; ++w) cnt[w] = 0;
-    uint32_t alive = valid;
+    for (int w = 0; w < 32; ++w) cnt[w] = (valid >> w) & 1u ? 0u : kPast;
     for (uint32_t c = 0; c < nchunks; ++c) {
         if (c > 0) {
             t0 = t1;
             t1 = __ldg(planes + blk + c + 1);
         }
         const uint4 Mc = __ldg(M + c);
-        uint32_t a2 = 0;
+        uint32_t low = kPast;
 #pragma unroll
         for (int w = 0; w < 32; ++w) {
             cnt[w] += __popc(~class_match(__funnelshift_r(t0.x, t1.x, w), __funnelshift_r(t0.y, t1.y, w), Mc));
-            a2 |= (cnt[w] <= k ? 1u : 0u) << w;
+            low = min(low, cnt[w]);
         }
-        alive &= a2;
-        if (!__any_sync(kFull, alive != 0u)) break;
+        if (!__any_sync(kFull, low <= k)) break;
     }
+    uint32_t alive = 0;
+#pragma unroll
+    for (int w = 0; w < 32; ++w) alive |= (cnt[w] <= k ? 1u : 0u) << w;
     return alive;
 }
 
